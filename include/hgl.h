@@ -1,0 +1,311 @@
+/*
+ * hgl.h -- C ABI of libhgl: adaptive hypergraph learning on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Karantaidis, Sarridis and Kotropoulos, "Block randomized optimization for
+ * adaptive hypergraph learning" (arXiv 1908.08281), Sections 2 and 3.
+ *
+ * Notation (the paper's Section 2 swaps the letters n and m):
+ *   n vertices, m hyperedges, c right-hand-side (tag) columns, nnz incidences;
+ *   H (n x m, 0/1) incidence; w (m) hyperedge weights; dv = H w; de = H^T 1;
+ *   Theta = Dv^-1/2 H W De^-1 H^T Dv^-1/2                          (Eq. 1, the paper's A)
+ *   Delta = I - Theta                                              (Zhou's Laplacian)
+ *   ranking system  M F = lam Y,  M = (1 + lam) I - Theta          (Eqs. 3 and 6 times 1+lam)
+ *   P(w) = tr(F^T Delta F) + mu ||w||^2,  1^T w = 1, w >= 0         (Eq. 4)
+ * A vertex with dv = 0 gets Dv^-1/2 = 0 (pseudo-inverse), so its row and column of
+ * Theta vanish.
+ *
+ * Conventions shared by every entry point
+ *   - Panels (X, Y, F, Z, ...) are caller-owned DEVICE memory, row-major n x c with a
+ *     leading dimension ld >= c (in elements); the base address must be 16-byte
+ *     aligned and ld * element_size a multiple of 16 bytes, else HGL_ERR_INVALID_ARG.
+ *     Columns c .. ld-1 are never written.
+ *   - Vectors (w, grad, dv, ...) are caller-owned device arrays of FP64.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls are ordered on that stream.  Entry points that return statistics to the
+ *     host synchronise the stream before returning; the others are asynchronous.
+ *   - Opaque handles (hgl_graph, hgl_precond) are library-owned: create/destroy pairs.
+ *     A handle holds device work buffers, so two calls on the same handle must not
+ *     run concurrently (on different streams or host threads).
+ *   - No exception crosses the ABI and nothing aborts.  A failed CUDA call returns
+ *     HGL_ERR_CUDA (or HGL_ERR_OOM) and hgl_last_error() describes it.
+ */
+#ifndef HGL_H_
+#define HGL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hgl_status;
+
+#define HGL_OK                    0
+#define HGL_ERR_INVALID_ARG      -1  /* bad size, pointer, alignment or option            */
+#define HGL_ERR_INDEX_RANGE      -2  /* a member vertex id outside [0, n)                  */
+#define HGL_ERR_DUPLICATE_MEMBER -3  /* a vertex listed twice in one hyperedge (H is 0/1)   */
+#define HGL_ERR_EMPTY_EDGE       -4  /* a hyperedge with no members (De^-1 undefined)       */
+#define HGL_ERR_OOM              -5  /* device allocation failed                            */
+#define HGL_ERR_CUDA             -6  /* a CUDA runtime call failed                          */
+#define HGL_ERR_NOT_CONVERGED    -7  /* an iteration reached its limit before its tolerance */
+#define HGL_ERR_TIMEOUT          -8  /* a device-side wait hit its spin limit               */
+#define HGL_ERR_NONFINITE        -9  /* NaN or Inf met in a reduction                       */
+
+/* Element type of a panel. */
+typedef enum {
+  HGL_FP64 = 0,
+  HGL_FP32 = 1,
+  HGL_BF16 = 2
+} hgl_dtype;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* hgl_status_string(hgl_status s);
+
+/* Text of the last error met by the calling host thread ("" if none). */
+const char* hgl_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t hgl_version(void);
+
+/* ------------------------------------------------------------------------- */
+/* Incidence (Section 2: H(v,e) = 1 iff v in e; de(e) = sum_v H(v,e))         */
+/* ------------------------------------------------------------------------- */
+
+typedef struct hgl_graph hgl_graph;
+
+/*
+ * hgl_build_incidence -- build the device incidence structure from member lists.
+ *   n, m       vertex and hyperedge counts (n >= 1, m >= 1, both < 2^31)
+ *   edge_ptr   int64[m+1], host or device: hyperedge e owns members[edge_ptr[e] ..
+ *              edge_ptr[e+1]); edge_ptr[0] = 0, non-decreasing, edge_ptr[m] = nnz
+ *   members    int32[nnz], host or device, any order inside a hyperedge
+ *   nnz        number of incidences (< 2^31)
+ *   out        receives a new handle on success (NULL on failure)
+ * Builds, bit-exactly and deterministically: the hyperedge-major layout (members of
+ * each hyperedge in ascending order), the vertex-major layout (hyperedges of each
+ * vertex in ascending order) and de.  Validation errors: HGL_ERR_INVALID_ARG
+ * (pointer array), HGL_ERR_EMPTY_EDGE, HGL_ERR_INDEX_RANGE, HGL_ERR_DUPLICATE_MEMBER.
+ * A vertex in no hyperedge is allowed.  Synchronises `stream`.
+ */
+hgl_status hgl_build_incidence(int64_t n, int64_t m, const int64_t* edge_ptr,
+                               const int32_t* members, int64_t nnz, void* stream,
+                               hgl_graph** out);
+
+/* Release a graph handle and all of its device memory (NULL is a no-op). */
+void hgl_graph_destroy(hgl_graph* g);
+
+/* Sizes of a graph (any output pointer may be NULL). */
+hgl_status hgl_graph_info(const hgl_graph* g, int64_t* n, int64_t* m, int64_t* nnz);
+
+/*
+ * hgl_graph_export -- copy the layouts into caller-owned DEVICE arrays (any may be
+ * NULL): csc_ptr int64[m+1], csc_idx int32[nnz] (hyperedge -> sorted members),
+ * csr_ptr int64[n+1], csr_idx int32[nnz] (vertex -> sorted hyperedges), de int32[m].
+ * Asynchronous on `stream`.
+ */
+hgl_status hgl_graph_export(const hgl_graph* g, int64_t* csc_ptr, int32_t* csc_idx,
+                            int64_t* csr_ptr, int32_t* csr_idx, int32_t* de, void* stream);
+
+/*
+ * hgl_degrees -- dv = H w, s = dv^-1/2 (0 where dv <= 0), t = w / de (Section 2,
+ * the scalings of Eq. 1).  w: device FP64[m]; outputs device FP64 dv[n], s[n],
+ * t[m] (any may be NULL).  Asynchronous.
+ */
+hgl_status hgl_degrees(const hgl_graph* g, const double* w, double* dv, double* s,
+                       double* t, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Operator (Eq. 1)                                                          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * hgl_apply_theta -- Z = a X + b Theta(w) X, applied matrix-free from H (Eq. 1);
+ * (a, b) = (1 + lam, -1) gives Z = M X.
+ *   w        device FP64[m] (w >= 0 expected; dv <= 0 gives s = 0)
+ *   X, Z     device panels n x c of type `dtype`, leading dimensions ldx, ldz; X and
+ *            Z must not overlap.  FP64 panels accumulate in FP64; FP32 and BF16
+ *            panels accumulate in FP32 (the intermediate m x c panel is FP32).
+ * Uses a graph-owned scratch panel of m x min(c, chunk) accumulators, allocated on
+ * first use.  Asynchronous.
+ */
+hgl_status hgl_apply_theta(const hgl_graph* g, const double* w, double a, double b,
+                           const void* X, int64_t ldx, void* Z, int64_t ldz, int32_t c,
+                           hgl_dtype dtype, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Solve (Eq. 6 by conjugate gradient, Eqs. 16-20)                           */
+/* ------------------------------------------------------------------------- */
+
+typedef struct hgl_precond hgl_precond;
+
+#define HGL_SOLVE_WARM_START 1   /* F holds the initial guess f_0 (else f_0 = 0) */
+
+typedef struct {
+  double  tol;         /* per-column target ||lam y_j - M f_j|| <= tol ||lam y_j||       */
+  int32_t max_iter;    /* cap on CG iterations (all refinement sweeps together)          */
+  int32_t dtype;       /* HGL_FP64: plain FP64 CG.  HGL_FP32 / HGL_BF16: CG on panels of */
+                       /* that type with FP32 arithmetic, inside FP64 iterative          */
+                       /* refinement (residual recomputed in FP64 from the FP64 F)       */
+  double  inner_tol;   /* mixed modes: relative reduction asked of each inner solve      */
+                       /* (0 = 1e-4 for FP32, 1e-2 for BF16)                             */
+  int32_t max_refine;  /* mixed modes: cap on refinement sweeps (0 = 8)                  */
+  int32_t flags;       /* HGL_SOLVE_WARM_START                                           */
+} hgl_solve_opts;
+
+typedef struct {
+  hgl_status status;     /* HGL_OK or HGL_ERR_NOT_CONVERGED / HGL_ERR_NONFINITE          */
+  int32_t iters;         /* CG iterations done (max over columns, all sweeps together)   */
+  int32_t refinements;   /* FP64 residual recomputations after the first (mixed modes)  */
+  int32_t converged;     /* number of columns that met tol                               */
+  double  relres_max;    /* max over columns of ||lam y_j - M f_j|| / ||lam y_j||,       */
+                         /* recomputed from the returned F in FP64                        */
+} hgl_solve_stats;
+
+/*
+ * hgl_cg_solve -- solve M F = lam Y for all c columns (independent CG per column).
+ *   w          device FP64[m];  lam > 0
+ *   Y          device FP64 panel n x c (ldy)
+ *   F          device FP64 panel n x c (ldf): initial guess if HGL_SOLVE_WARM_START,
+ *              solution on return
+ *   precond    NULL, or a block preconditioner from hgl_block_rsvd built for this
+ *              graph (then the recurrences are those of preconditioned CG)
+ *   relres     optional device FP64[c]: per-column final relative residual
+ *   iters      optional device int32[c]: per-column iteration count
+ *   stats      optional host struct
+ * A zero column of Y gives F_j = 0.  Returns HGL_ERR_NOT_CONVERGED if some column
+ * missed tol within max_iter (F then holds the last iterate).  Synchronises `stream`.
+ */
+hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double lam, const double* Y,
+                        int64_t ldy, double* F, int64_t ldf, int32_t c,
+                        const hgl_precond* precond, const hgl_solve_opts* opts,
+                        double* relres, int32_t* iters, hgl_solve_stats* stats,
+                        void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Block randomized SVD (Section 3, Algorithm 1) as a block preconditioner   */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * hgl_block_rsvd -- tessellate the vertex range into contiguous diagonal blocks
+ * [block_ptr[b], block_ptr[b+1]) (Section 3) and approximate each dense Theta_bb by
+ * randomized subspace iteration (Algorithm 1) with l = k + p columns and q
+ * iterations: Y0 = Theta_bb Omega, then q times two products each followed by an
+ * orthonormalisation (CholeskyQR2), then the Rayleigh-Ritz factorisation
+ * Theta_bb ~= Q_b diag(ev_b) Q_b^T (top k).  The handle then applies
+ *   z_b = r_b / (1+lam) + Q_b diag(ev/((1+lam)(1+lam-ev))) Q_b^T r_b,
+ * the inverse of M_bb = (1+lam) I - Theta_bb on the captured subspace (Eq. 15 with the
+ * identity part of M kept).
+ *   block_ptr  HOST int64[nblocks+1], 0 = block_ptr[0] < ... < block_ptr[nblocks] = n
+ *   k, p, q    rank, oversampling, iterations (k >= 1, p >= 0, q >= 0)
+ *   seed       seed of the Philox4x32-10 Gaussian test matrix Omega (see below)
+ *   gemm_dtype HGL_BF16: Theta_bb and the bases in BF16, products on the tcgen05
+ *              tensor cores with FP32 accumulation; HGL_FP64: all products in FP64
+ *              on the CUDA cores (slow; for checking)
+ * Omega[g, j] for global vertex row g and column j: x = Philox4x32-10(counter
+ * (g, j>>1, 0x4F6D6567, 0), key (seed & 0xffffffff, seed >> 32)); u1, u2 in (0,1) from
+ * (x0,x1) and (x2,x3) as ((hi>>5)*2^26 + (lo>>6) + 1/2) * 2^-53; Omega = sqrt(-2 ln u1)
+ * times cos(2 pi u2) for even j, sin(2 pi u2) for odd j (Box-Muller).
+ * Synchronises `stream`.
+ */
+hgl_status hgl_block_rsvd(const hgl_graph* g, const double* w, double lam,
+                          const int64_t* block_ptr, int32_t nblocks, int32_t k, int32_t p,
+                          int32_t q, uint64_t seed, hgl_dtype gemm_dtype, void* stream,
+                          hgl_precond** out);
+
+/* Release a preconditioner (NULL is a no-op). */
+void hgl_precond_destroy(hgl_precond* P);
+
+/*
+ * hgl_precond_export -- copy block b's factors to caller-owned DEVICE FP64 arrays:
+ * Q row-major (block size) x k and ev[k] (descending).  kb receives the block's rank
+ * (min(k, block size)).  Asynchronous.
+ */
+hgl_status hgl_precond_export(const hgl_precond* P, int32_t b, double* Q, double* ev,
+                              int32_t* kb, void* stream);
+
+/*
+ * hgl_precond_apply -- Z = P^-1 R (formula above) for device panels of `dtype`
+ * (FP64 or FP32), n x c.  Asynchronous.
+ */
+hgl_status hgl_precond_apply(const hgl_precond* P, const void* R, int64_t ldr, void* Z,
+                             int64_t ldz, int32_t c, hgl_dtype dtype, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Weight update (Section 2, Eqs. 4 and 5)                                   */
+/* ------------------------------------------------------------------------- */
+
+#define HGL_GRAD_DV_FROZEN 1   /* differentiate only the explicit W De^-1 factor */
+
+/*
+ * hgl_weight_grad -- grad = -d tr(Z^T Theta(w) F) / dw + 2 mu w, at fixed F and Z.
+ * With Z = NULL (Z = F) this is grad_w P(w) of Eq. 4.  The derivative includes the
+ * dependence of dv on w (Section 2 defines dv through w):
+ *   d/dw_e tr(Z^T Theta F) = <sF_e, sZ_e>/de_e
+ *        - 1/2 sum_{v in e} (1/dv_v) (<G_v, UZ_v> + <R_v, UF_v>),
+ *   G = Dv^-1/2 F, R = Dv^-1/2 Z, sF = H^T G, sZ = H^T R, UX = H diag(w/de) sX.
+ *   F, Z       device panels n x c of `dtype` (FP64 or FP32), leading dimension ld
+ *   grad       device FP64[m]
+ * flags: HGL_GRAD_DV_FROZEN keeps only the first term.  Asynchronous.
+ */
+hgl_status hgl_weight_grad(const hgl_graph* g, const double* w, const void* F,
+                           const void* Z, int64_t ld, int32_t c, hgl_dtype dtype,
+                           double mu, int32_t flags, double* grad, void* stream);
+
+/*
+ * hgl_project_simplex -- w <- argmin_{u >= 0, 1^T u = 1} ||u - (w - eta grad)||,
+ * the constrained steepest-descent step of Eq. 5 read as a Euclidean projection.
+ * The threshold tau with sum_e max(v_e - tau, 0) = 1 is found by Michelot's
+ * support-shrinking iteration, then w_e = max(v_e - tau, 0).
+ *   w          device FP64[m], in/out;  grad device FP64[m] (NULL = zero)
+ * Asynchronous.
+ */
+hgl_status hgl_project_simplex(double* w, const double* grad, double eta, int64_t m,
+                               void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Adaptive outer iteration (Section 2: F at fixed w, then w at fixed F)      */
+/* ------------------------------------------------------------------------- */
+
+#define HGL_ROUTE_CG 0   /* plain CG solve (CG-ITH-HWEG, Section 4)                     */
+#define HGL_ROUTE_BR 1   /* CG preconditioned by the block rSVD (BR-ITH-HWEG)          */
+
+#define HGL_STEP_GRAPH 1 /* replay the step as one captured CUDA graph                 */
+
+typedef struct {
+  double  lam;           /* ranking regulariser (theta of Eq. 3), > 0                     */
+  double  mu;            /* weight regulariser (kappa of Eq. 4), >= 0                     */
+  double  eta;           /* step size of the projected gradient step                     */
+  int32_t route;         /* HGL_ROUTE_CG or HGL_ROUTE_BR                                 */
+  int32_t flags;         /* HGL_STEP_GRAPH                                               */
+  hgl_solve_opts solve;  /* inner solve options (warm start from F is always used)       */
+  const int64_t* block_ptr; int32_t nblocks;   /* HGL_ROUTE_BR: host block boundaries     */
+  int32_t k, p, q;       /* HGL_ROUTE_BR: rank, oversampling, iterations                  */
+  uint64_t seed;         /* HGL_ROUTE_BR: Omega seed                                      */
+} hgl_step_opts;
+
+typedef struct {
+  hgl_solve_stats solve;
+  double objective;      /* P(w) = tr(F^T Delta F) + mu ||w||^2 at the solve's w and F    */
+  double dw_norm;        /* ||w_new - w_old||_2                                           */
+} hgl_step_stats;
+
+/*
+ * hgl_adaptive_step -- one outer iteration of the alternation:
+ *   1. degrees from w;  [route BR: block rSVD preconditioner at this w]
+ *   2. solve M(w) F = lam Y, warm-started from F;
+ *   3. grad = grad_w P(w) at that F (hgl_weight_grad with Z = F);
+ *   4. w <- projection of w - eta grad onto the simplex.
+ *   g          graph;  w device FP64[m] in/out;  Y device FP64 panel (ldy);
+ *   F          device FP64 panel (ldf), in: warm start, out: the solve of step 2
+ * Synchronises `stream` (statistics).
+ */
+hgl_status hgl_adaptive_step(hgl_graph* g, double* w, const hgl_step_opts* opts,
+                             const double* Y, int64_t ldy, double* F, int64_t ldf,
+                             int32_t c, hgl_step_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGL_H_ */

@@ -1,0 +1,165 @@
+// api.cu -- status strings, error recording, work buffers, graph queries and the
+// degree/scaling kernel (Section 2: dv = H w, de = H^T 1; Eq. 1 scalings).
+#include <cstdarg>
+#include <cstring>
+
+#include "hgl_internal.cuh"
+
+namespace hgl {
+
+static thread_local char g_last_error[512] = "";
+
+hgl_status record_error(hgl_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  const char* f = strrchr(file, '/');
+  f = f ? f + 1 : file;
+  record_error(e == cudaErrorMemoryAllocation ? HGL_ERR_OOM : HGL_ERR_CUDA, "%s failed: %s (%s:%d)", what,
+               cudaGetErrorString(e), f, line);
+  return e == cudaErrorMemoryAllocation ? HGL_ERR_OOM : HGL_ERR_CUDA;
+}
+
+void* buffer_get(Buffer& b, size_t bytes, hgl_status* st) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return b.ptr;
+  if (b.ptr) {
+    cudaError_t e = cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    if (e != cudaSuccess) {
+      *st = cuda_error(e, "cudaFree(work buffer)", __FILE__, __LINE__);
+      return nullptr;
+    }
+  }
+  size_t want = bytes + bytes / 8;  // headroom for slightly larger later calls
+  cudaError_t e = cudaMalloc(&b.ptr, want);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    b.ptr = nullptr;
+    *st = cuda_error(e, "cudaMalloc(work buffer)", __FILE__, __LINE__);
+    return nullptr;
+  }
+  b.bytes = want;
+  return b.ptr;
+}
+
+void buffer_free(Buffer& b) {
+  if (b.ptr) cudaFree(b.ptr);
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+// dv_v = sum_{e in row v} w_e (row order), s_v = dv^-1/2 or 0;  t_e = w_e / de_e.
+__global__ void k_degrees(int64_t n, int64_t m, const int64_t* __restrict__ csr_ptr,
+                          const int32_t* __restrict__ csr_idx, const int32_t* __restrict__ de,
+                          const double* __restrict__ w, double* __restrict__ dv,
+                          double* __restrict__ s, double* __restrict__ t) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+    double acc = 0.0;
+    for (int64_t i = csr_ptr[v], end = csr_ptr[v + 1]; i < end; ++i) acc += w[csr_idx[i]];
+    dv[v] = acc;
+    s[v] = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
+    t[e] = w[e] / (double)de[e];
+}
+
+hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st) {
+  int blocks = g->num_sms * 8;
+  k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+}  // namespace hgl
+
+extern "C" {
+
+const char* hgl_status_string(hgl_status s) {
+  switch (s) {
+    case HGL_OK: return "HGL_OK";
+    case HGL_ERR_INVALID_ARG: return "HGL_ERR_INVALID_ARG";
+    case HGL_ERR_INDEX_RANGE: return "HGL_ERR_INDEX_RANGE";
+    case HGL_ERR_DUPLICATE_MEMBER: return "HGL_ERR_DUPLICATE_MEMBER";
+    case HGL_ERR_EMPTY_EDGE: return "HGL_ERR_EMPTY_EDGE";
+    case HGL_ERR_OOM: return "HGL_ERR_OOM";
+    case HGL_ERR_CUDA: return "HGL_ERR_CUDA";
+    case HGL_ERR_NOT_CONVERGED: return "HGL_ERR_NOT_CONVERGED";
+    case HGL_ERR_TIMEOUT: return "HGL_ERR_TIMEOUT";
+    case HGL_ERR_NONFINITE: return "HGL_ERR_NONFINITE";
+    default: return "HGL_ERR_UNKNOWN";
+  }
+}
+
+const char* hgl_last_error(void) { return hgl::g_last_error; }
+
+int32_t hgl_version(void) { return 100; }
+
+void hgl_graph_destroy(hgl_graph* g) {
+  if (!g) return;
+  cudaFree(g->csc_ptr);
+  cudaFree(g->csc_idx);
+  cudaFree(g->csr_ptr);
+  cudaFree(g->csr_idx);
+  cudaFree(g->de);
+  cudaFree(g->dv);
+  cudaFree(g->s);
+  cudaFree(g->t);
+  hgl::buffer_free(g->scratch);
+  hgl::buffer_free(g->scratch2);
+  hgl::buffer_free(g->partials);
+  hgl::buffer_free(g->solver);
+  hgl::buffer_free(g->misc);
+  hgl::buffer_free(g->step);
+  delete g;
+}
+
+hgl_status hgl_graph_info(const hgl_graph* g, int64_t* n, int64_t* m, int64_t* nnz) {
+  if (!g) return hgl::record_error(HGL_ERR_INVALID_ARG, "graph is NULL");
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (nnz) *nnz = g->nnz;
+  return HGL_OK;
+}
+
+hgl_status hgl_graph_export(const hgl_graph* g, int64_t* csc_ptr, int32_t* csc_idx, int64_t* csr_ptr,
+                            int32_t* csr_idx, int32_t* de, void* stream) {
+  if (!g) return hgl::record_error(HGL_ERR_INVALID_ARG, "graph is NULL");
+  cudaStream_t st = hgl::as_stream(stream);
+  if (csc_ptr)
+    HGL_CHECK_CUDA(cudaMemcpyAsync(csc_ptr, g->csc_ptr, sizeof(int64_t) * (g->m + 1), cudaMemcpyDeviceToDevice, st));
+  if (csc_idx)
+    HGL_CHECK_CUDA(cudaMemcpyAsync(csc_idx, g->csc_idx, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToDevice, st));
+  if (csr_ptr)
+    HGL_CHECK_CUDA(cudaMemcpyAsync(csr_ptr, g->csr_ptr, sizeof(int64_t) * (g->n + 1), cudaMemcpyDeviceToDevice, st));
+  if (csr_idx)
+    HGL_CHECK_CUDA(cudaMemcpyAsync(csr_idx, g->csr_idx, sizeof(int32_t) * g->nnz, cudaMemcpyDeviceToDevice, st));
+  if (de) HGL_CHECK_CUDA(cudaMemcpyAsync(de, g->de, sizeof(int32_t) * g->m, cudaMemcpyDeviceToDevice, st));
+  return HGL_OK;
+}
+
+hgl_status hgl_degrees(const hgl_graph* g, const double* w, double* dv, double* s, double* t, void* stream) {
+  if (!g || !w) return hgl::record_error(HGL_ERR_INVALID_ARG, "graph or w is NULL");
+  cudaStream_t st = hgl::as_stream(stream);
+  HGL_TRY(hgl::degrees_launch(g, w, st));
+  if (dv) HGL_CHECK_CUDA(cudaMemcpyAsync(dv, g->dv, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, st));
+  if (s) HGL_CHECK_CUDA(cudaMemcpyAsync(s, g->s, sizeof(double) * g->n, cudaMemcpyDeviceToDevice, st));
+  if (t) HGL_CHECK_CUDA(cudaMemcpyAsync(t, g->t, sizeof(double) * g->m, cudaMemcpyDeviceToDevice, st));
+  return HGL_OK;
+}
+
+}  // extern "C"

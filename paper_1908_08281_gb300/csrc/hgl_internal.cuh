@@ -1,0 +1,120 @@
+// hgl_internal.cuh -- shared internals of libhgl (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/hgl.h"
+
+// A graph handle: the two compressed layouts of H plus per-graph work buffers.
+// Work buffers grow on demand and are reused; calls on one handle are serial.
+namespace hgl {
+
+struct Buffer {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// Returns a device buffer of at least `bytes` (contents undefined), or nullptr after
+// recording HGL_ERR_OOM / HGL_ERR_CUDA in *st.
+void* buffer_get(Buffer& b, size_t bytes, hgl_status* st);
+void buffer_free(Buffer& b);
+
+hgl_status record_error(hgl_status s, const char* fmt, ...);
+hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+int device_sm_count();
+
+}  // namespace hgl
+
+struct hgl_graph {
+  int64_t n = 0, m = 0, nnz = 0;
+  int device = 0;
+  int num_sms = 0;
+  int64_t* csc_ptr = nullptr;  // m+1
+  int32_t* csc_idx = nullptr;  // nnz, members of each hyperedge ascending
+  int64_t* csr_ptr = nullptr;  // n+1
+  int32_t* csr_idx = nullptr;  // nnz, hyperedges of each vertex ascending
+  int32_t* de = nullptr;       // m
+  double* dv = nullptr;        // n   (for the w of the last degrees call)
+  double* s = nullptr;         // n   dv^-1/2 (0 where dv <= 0)
+  double* t = nullptr;         // m   w / de
+  hgl::Buffer scratch;         // m x chunk intermediate panel of the operator
+  hgl::Buffer scratch2;        // second intermediate panel (bilinear gradient)
+  hgl::Buffer partials;        // per-block reduction partials
+  hgl::Buffer solver;          // CG panels and per-column state
+  hgl::Buffer misc;            // gradient vectors (ex[m], phi[n])
+  hgl::Buffer step;            // adaptive-step vectors (grad, w_old, projection work)
+  int chunk_cols = 0;          // operator column chunk (0 = library default)
+};
+
+#define HGL_CHECK_CUDA(call)                                                   \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) return ::hgl::cuda_error(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HGL_TRY(expr)                      \
+  do {                                     \
+    hgl_status s_ = (expr);                \
+    if (s_ != HGL_OK) return s_;           \
+  } while (0)
+
+namespace hgl {
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Panel argument check: device pointer 16-byte aligned, ld >= c, ld * elt % 16 == 0.
+inline hgl_status check_panel(const void* p, int64_t ld, int32_t c, size_t elt, const char* name) {
+  if (p == nullptr) return record_error(HGL_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!aligned16(p)) return record_error(HGL_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  if (ld < c) return record_error(HGL_ERR_INVALID_ARG, "leading dimension of %s is below c", name);
+  if ((ld * (int64_t)elt) % 16 != 0)
+    return record_error(HGL_ERR_INVALID_ARG, "leading dimension of %s times element size is not a multiple of 16 bytes", name);
+  return HGL_OK;
+}
+
+inline size_t dtype_size(int dt) { return dt == HGL_FP64 ? 8 : (dt == HGL_FP32 ? 4 : 2); }
+
+// ---------------------------------------------------------------------------
+// operator internals (theta.cu)
+// ---------------------------------------------------------------------------
+
+// Epilogues of the vertex pass of the operator.
+enum Epilogue : int {
+  EPI_PLAIN = 0,   // Z = a X + b s (H T)
+  EPI_DOT_XZ = 1,  // same, plus per-column partial sums of X.Z      (CG: p^T M p)
+  EPI_RESID = 2,   // Z = gy Y + a X + b s (H T), plus partial sums of Z.Z (residual)
+};
+
+struct OpCall {
+  const hgl_graph* g;
+  int xdt;          // element type of X (HGL_FP64/FP32/BF16)
+  int zdt;          // element type of Z
+  const void* X; int64_t ldx;
+  void* Z; int64_t ldz;
+  int32_t c;
+  double a, b;
+  int epi;
+  const double* Y; int64_t ldy; double gy;   // EPI_RESID only (FP64 Y)
+  double* partials;  // EPI_DOT_XZ / EPI_RESID: [grid2 x c] FP64 partial sums (row stride c)
+  const int32_t* run_flag;  // optional device flag: kernels return at once when *run_flag == 0
+  int chunk_cols;   // 0 = default column chunk
+};
+
+// Launch both passes of the operator over all column chunks.  Returns the number of
+// blocks of the vertex pass (the row count of `partials`) in *grid2.
+hgl_status op_launch(const OpCall& call, cudaStream_t st, int* grid2);
+
+// Blocks the vertex pass will use (for sizing `partials`).
+int op_partial_rows(const hgl_graph* g);
+
+// Recompute dv, s, t for w into the graph's vectors.
+hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st);
+
+}  // namespace hgl

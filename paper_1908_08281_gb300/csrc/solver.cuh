@@ -1,0 +1,50 @@
+// solver.cuh -- internals shared by the CG solver, the preconditioner and the
+// adaptive step.
+#pragma once
+
+#include "hgl_internal.cuh"
+#include "vec_kernels.cuh"
+
+namespace hgl {
+
+struct VecGrid {
+  int lg = 32, gx = 1, gy = 1;
+};
+
+// Launch shape of the row-parallel panel kernels for c columns of `elt`-byte elements.
+VecGrid vec_grid(const hgl_graph* g, int c, int elt);
+
+struct SolverMem {
+  CgState S{};
+  void* R = nullptr;  // residual
+  void* P = nullptr;  // search direction
+  void* Q = nullptr;  // M p
+  void* Z = nullptr;  // preconditioned residual
+  void* X = nullptr;  // mixed modes: correction D
+  double* pa = nullptr;
+  double* pb = nullptr;
+  int c = 0;
+  int64_t ld64 = 0, ld32 = 0, ld16 = 0;
+  void* int_base = nullptr;  // per-column int32 state and flags (zeroed per solve)
+  size_t int_bytes = 0;
+};
+
+hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
+
+hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double* Y, int64_t ldy, double* F,
+                         int64_t ldf, int c, const hgl_precond* P, const hgl_solve_opts& o, double* relres_out,
+                         int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready);
+
+int cg_iteration_bound(double lam, double tol);
+
+// sum over all entries of F*F (FP64 panel), deterministic; synchronises the stream.
+hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out);
+
+// Preconditioner hooks (rsvd.cu).  Z = P^-1 R on panels of `dt` (FP64 or FP32) and,
+// when partials_rz is given, per-column partial sums of R.Z (row count in *rows).
+hgl_status precond_check(const hgl_precond* P, const hgl_graph* g, double lam);
+hgl_status precond_apply_launch(const hgl_precond* P, const hgl_graph* g, const void* R, int64_t ldr, void* Z,
+                                int64_t ldz, int c, int dt, double* partials_rz, cudaStream_t st, int* rows,
+                                const int32_t* run_flag);
+
+}  // namespace hgl

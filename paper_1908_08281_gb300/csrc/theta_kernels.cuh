@@ -1,0 +1,228 @@
+// theta_kernels.cuh -- the two gather passes that apply Theta (Eq. 1) matrix-free.
+//
+//   hyperedge pass:  T[e, :] = t_e * sum_{v in e} s_v X[v, :]           (W De^-1 H^T Dv^-1/2 X)
+//   vertex pass:     Z[v, :] = a X[v, :] + b s_v sum_{e ni v} T[e, :]   (+ gy Y[v, :])
+//
+// with s = dv^-1/2 and t = w / de.  Both passes are row gathers over the compressed
+// layouts: one warp owns one output row at a time; the warp is split into G = 32/LG
+// groups of LG lanes, each group reads one input row per step (16-byte vector loads,
+// NV vectors per lane), and the groups are summed with a shuffle butterfly.  The
+// right-hand-side columns are processed in chunks of LG*NV*E columns (E elements
+// per 16 bytes) so that the gathered slice of X can stay in L2 across the pass.
+#pragma once
+
+#include "hgl_internal.cuh"
+#include "panel.cuh"
+
+namespace hgl {
+
+constexpr int OP_THREADS = 256;
+constexpr int OP_WARPS = OP_THREADS / 32;
+
+template <class TX, class TT, int LG, int NV>
+__global__ void __launch_bounds__(OP_THREADS)
+k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
+            const double* __restrict__ s, const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx,
+            int c0, int cw, TT* __restrict__ Tp, int64_t ldt, const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
+  using A = typename AccOf<TX>::type;
+  constexpr int E = 16 / (int)sizeof(TX);
+  constexpr int G = 32 / LG;
+  constexpr int U = 2;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const TX* Xc = X + c0;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int64_t beg = __ldg(csc_ptr + e), end = __ldg(csc_ptr + e + 1);
+    A acc[NV][E];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc[k][j] = A(0);
+    int64_t i = beg + grp;
+    for (; i + (U - 1) * G < end; i += U * G) {
+      int32_t v[U];
+      A sv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = __ldg(csc_idx + i + u * G);
+#pragma unroll
+      for (int u = 0; u < U; ++u) sv[u] = (A)__ldg(s + v[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          const int col = (k * LG + l) * E;
+          if (col < cw) {
+            A x[E];
+            vload<A, TX, E>(Xc + (int64_t)v[u] * ldx + col, x);
+#pragma unroll
+            for (int j = 0; j < E; ++j) acc[k][j] = fma(sv[u], x[j], acc[k][j]);
+          }
+        }
+    }
+    for (; i < end; i += G) {
+      const int32_t v = __ldg(csc_idx + i);
+      const A sv = (A)__ldg(s + v);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, TX, E>(Xc + (int64_t)v * ldx + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) acc[k][j] = fma(sv, x[j], acc[k][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[k][j] += __shfl_xor_sync(0xffffffffu, acc[k][j], off);
+    if (grp == 0) {
+      const A te = (A)__ldg(t + e);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A o[E];
+#pragma unroll
+          for (int j = 0; j < E; ++j) o[j] = te * acc[k][j];
+          vstore<TT, A, E>(Tp + e * ldt + col, o, E);
+        }
+      }
+    }
+  }
+}
+
+template <class TX, class TT, class TZ, int LG, int NV, int EPI>
+__global__ void __launch_bounds__(OP_THREADS)
+k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+              const double* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
+              int64_t ldx, TZ* __restrict__ Z, int64_t ldz, int c0, int cw, int c, double a, double b,
+              const double* __restrict__ Y, int64_t ldy, double gy, double* __restrict__ partials,
+              const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
+  using A = typename AccOf<TX>::type;
+  constexpr int E = 16 / (int)sizeof(TX);
+  constexpr int G = 32 / LG;
+  constexpr int U = 2;
+  constexpr int TILE = LG * NV * E;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
+  const int wid = threadIdx.x >> 5;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const A aa = (A)a, bb = (A)b;
+  DotAcc<A> dot[NV][E];
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t beg = __ldg(csr_ptr + v), end = __ldg(csr_ptr + v + 1);
+    A acc[NV][E];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc[k][j] = A(0);
+    int64_t i = beg + grp;
+    for (; i + (U - 1) * G < end; i += U * G) {
+      int32_t e[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) e[u] = __ldg(csr_idx + i + u * G);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          const int col = (k * LG + l) * E;
+          if (col < cw) {
+            A x[E];
+            vload<A, TT, E>(Tp + (int64_t)e[u] * ldt + col, x);
+#pragma unroll
+            for (int j = 0; j < E; ++j) acc[k][j] += x[j];
+          }
+        }
+    }
+    for (; i < end; i += G) {
+      const int32_t e = __ldg(csr_idx + i);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, TT, E>(Tp + (int64_t)e * ldt + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) acc[k][j] += x[j];
+        }
+      }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[k][j] += __shfl_xor_sync(0xffffffffu, acc[k][j], off);
+    if (grp == 0) {
+      const A sb = bb * (A)__ldg(s + v);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E], z[E];
+          vload<A, TX, E>(X + v * ldx + c0 + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) z[j] = fma(aa, x[j], sb * acc[k][j]);
+          if constexpr (EPI == EPI_RESID) {
+            double y[E];
+            const int nv = cw - col < E ? cw - col : E;
+            for (int j = 0; j < E; ++j) y[j] = j < nv ? Y[v * ldy + c0 + col + j] : 0.0;
+#pragma unroll
+            for (int j = 0; j < E; ++j) z[j] = (A)((double)z[j] + gy * y[j]);
+          }
+          const int nvalid = cw - col;
+          vstore<TZ, A, E>(Z + v * ldz + c0 + col, z, nvalid);
+          if constexpr (EPI == EPI_DOT_XZ) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) dot[k][j].add(x[j], z[j]);
+          } else if constexpr (EPI == EPI_RESID) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) dot[k][j].add(z[j], z[j]);
+          }
+        }
+      }
+    }
+  }
+  if constexpr (EPI != EPI_PLAIN) {
+    // deterministic block reduction: warps add their column partials in turn
+    __shared__ double red[TILE];
+    for (int q = threadIdx.x; q < TILE; q += blockDim.x) red[q] = 0.0;
+    __syncthreads();
+    for (int w = 0; w < OP_WARPS; ++w) {
+      if (wid == w && grp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+          for (int j = 0; j < E; ++j) red[(k * LG + l) * E + j] += dot[k][j].value();
+      }
+      __syncthreads();
+    }
+    for (int q = threadIdx.x; q < cw && q < TILE; q += blockDim.x) partials[(int64_t)blockIdx.x * c + c0 + q] = red[q];
+  }
+}
+
+// (LG, NV) configurations compiled for every kernel family.
+#define HGL_FOR_EACH_TILE(X) X(1, 1) X(2, 1) X(4, 1) X(8, 1) X(16, 1) X(32, 1) X(32, 2) X(32, 4)
+
+// Pick (LG, NV) for a chunk of `vecs` 16-byte vectors per row (vecs >= 1):
+// LG = min(32, next power of two), NV = ceil(vecs / 32) rounded up to 1, 2 or 4.
+inline void pick_tile(int vecs, int* lg, int* nv) {
+  if (vecs <= 32) {
+    int p = 1;
+    while (p < vecs) p <<= 1;
+    *lg = p;
+    *nv = 1;
+  } else {
+    *lg = 32;
+    *nv = vecs <= 64 ? 2 : 4;
+  }
+}
+
+}  // namespace hgl

@@ -1,0 +1,67 @@
+// theta_launch.cuh -- host-side launch of the two operator passes over column chunks.
+#pragma once
+
+#include "theta_kernels.cuh"
+
+namespace hgl {
+
+// Default chunk width in 16-byte vectors per row (512 bytes of X per row).
+inline int default_chunk_vecs() { return 32; }
+
+inline int edge_grid(const hgl_graph* g) {
+  int64_t need = (g->m + OP_WARPS - 1) / OP_WARPS;
+  int64_t cap = (int64_t)g->num_sms * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+inline int vertex_grid(const hgl_graph* g) {
+  int64_t need = (g->n + OP_WARPS - 1) / OP_WARPS;
+  int64_t cap = (int64_t)g->num_sms * 8;
+  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+template <class TX, class TT, class TZ, int EPI>
+hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
+  hgl_graph* g = const_cast<hgl_graph*>(cl.g);
+  constexpr int E = 16 / (int)sizeof(TX);
+  const int nvec = (cl.c + E - 1) / E;
+  int chunk_vec = cl.chunk_cols > 0 ? (cl.chunk_cols + E - 1) / E : default_chunk_vecs();
+  if (chunk_vec > nvec) chunk_vec = nvec;
+  if (chunk_vec < 1) chunk_vec = 1;
+  int lg = 1, nv = 1;
+  pick_tile(chunk_vec, &lg, &nv);
+  const int cc = lg * nv * E;
+  hgl_status stt = HGL_OK;
+  TT* Tp = static_cast<TT*>(buffer_get(g->scratch, sizeof(TT) * (size_t)g->m * (size_t)cc, &stt));
+  if (!Tp) return stt;
+  const int grid1 = edge_grid(g), grid2 = vertex_grid(g);
+  const TX* X = static_cast<const TX*>(cl.X);
+  TZ* Z = static_cast<TZ*>(cl.Z);
+  for (int c0 = 0; c0 < cl.c; c0 += cc) {
+    const int cw = cl.c - c0 < cc ? cl.c - c0 : cc;
+#define HGL_EDGE_CASE(LG_, NV_)                                                                       \
+  else if (lg == LG_ && nv == NV_) k_edge_pass<TX, TT, LG_, NV_><<<grid1, OP_THREADS, 0, st>>>(          \
+      g->m, g->csc_ptr, g->csc_idx, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);
+#define HGL_VERTEX_CASE(LG_, NV_)                                                                     \
+  else if (lg == LG_ && nv == NV_) k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
+      g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
+      cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
+    if (false) {
+    }
+    HGL_FOR_EACH_TILE(HGL_EDGE_CASE)
+    if (false) {
+    }
+    HGL_FOR_EACH_TILE(HGL_VERTEX_CASE)
+#undef HGL_EDGE_CASE
+#undef HGL_VERTEX_CASE
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
+  if (grid2_out) *grid2_out = grid2;
+  return HGL_OK;
+}
+
+hgl_status op_launch_fp64(const OpCall& cl, cudaStream_t st, int* grid2);
+hgl_status op_launch_fp32(const OpCall& cl, cudaStream_t st, int* grid2);
+hgl_status op_launch_bf16(const OpCall& cl, cudaStream_t st, int* grid2);
+
+}  // namespace hgl

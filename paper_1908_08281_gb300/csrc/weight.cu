@@ -1,0 +1,422 @@
+// weight.cu -- the weight sub-problem of Section 2 (Eqs. 4 and 5): the gradient of
+// P(w) = tr(F^T Delta F) + mu ||w||^2 at fixed F, and the projected steepest-descent
+// step onto the simplex {w >= 0, 1^T w = 1}.
+//
+// Gradient (bilinear form, Z = F for P):
+//   d/dw_e tr(Z^T Theta F) = <sF_e, sZ_e>/de_e - sum_{v in e} phi_v,
+//   sX_e = sum_{v in e} s_v X[v,:]           (H^T Dv^-1/2 X, row e)
+//   UX_v = sum_{e ni v} t_e sX_e             (H W De^-1 H^T Dv^-1/2 X, row v)
+//   phi_v = 1/2 s_v^3 (<F_v, UZ_v> + <Z_v, UF_v>)     (from d dv_v / d w_e = H(v,e))
+// computed by a hyperedge gather pass (sX, and T = t sX for the next pass), a vertex
+// gather pass (phi) and a scalar hyperedge pass; columns are processed in chunks and
+// the row dot products are accumulated chunk by chunk in FP64.
+#include <algorithm>
+#include <vector>
+
+#include "solver.cuh"
+#include "theta_kernels.cuh"
+
+namespace hgl {
+
+namespace {
+
+template <class TX, int LG, int NV, bool DUAL>
+__global__ void __launch_bounds__(OP_THREADS)
+k_grad_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
+            const double* __restrict__ s, const double* __restrict__ t, const TX* __restrict__ F,
+            const TX* __restrict__ Zb, int64_t ld, int c0, int cw, typename AccOf<TX>::type* __restrict__ TF,
+            typename AccOf<TX>::type* __restrict__ TZ, int64_t ldt, double* __restrict__ ex) {
+  using A = typename AccOf<TX>::type;
+  constexpr int E = 16 / (int)sizeof(TX);
+  constexpr int G = 32 / LG;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    const int64_t beg = csc_ptr[e], end = csc_ptr[e + 1];
+    A sf[NV][E], sz[NV][E];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int j = 0; j < E; ++j) sf[k][j] = sz[k][j] = A(0);
+    for (int64_t i = beg + grp; i < end; i += G) {
+      const int32_t v = __ldg(csc_idx + i);
+      const A sv = (A)__ldg(s + v);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, TX, E>(F + (int64_t)v * ld + c0 + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) sf[k][j] = fma(sv, x[j], sf[k][j]);
+          if (DUAL) {
+            vload<A, TX, E>(Zb + (int64_t)v * ld + c0 + col, x);
+#pragma unroll
+            for (int j = 0; j < E; ++j) sz[k][j] = fma(sv, x[j], sz[k][j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          sf[k][j] += __shfl_xor_sync(0xffffffffu, sf[k][j], off);
+          if (DUAL) sz[k][j] += __shfl_xor_sync(0xffffffffu, sz[k][j], off);
+        }
+    double d = 0.0;
+    const A te = (A)t[e];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const int col = (k * LG + l) * E;
+      if (col < cw) {
+        A o[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          d += (double)sf[k][j] * (double)(DUAL ? sz[k][j] : sf[k][j]);
+          o[j] = te * sf[k][j];
+        }
+        if (grp == 0) {
+          vstore<A, A, E>(TF + e * ldt + col, o, E);
+          if (DUAL) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) o[j] = te * sz[k][j];
+            vstore<A, A, E>(TZ + e * ldt + col, o, E);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < LG; off <<= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) ex[e] = (c0 == 0 ? 0.0 : ex[e]) + d;
+  }
+}
+
+template <class TX, int LG, int NV, bool DUAL>
+__global__ void __launch_bounds__(OP_THREADS)
+k_grad_vertex(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+              const double* __restrict__ s, const typename AccOf<TX>::type* __restrict__ TF,
+              const typename AccOf<TX>::type* __restrict__ TZ, int64_t ldt, const TX* __restrict__ F,
+              const TX* __restrict__ Zb, int64_t ld, int c0, int cw, double* __restrict__ phi) {
+  using A = typename AccOf<TX>::type;
+  constexpr int E = 16 / (int)sizeof(TX);
+  constexpr int G = 32 / LG;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t beg = csr_ptr[v], end = csr_ptr[v + 1];
+    A uf[NV][E], uz[NV][E];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int j = 0; j < E; ++j) uf[k][j] = uz[k][j] = A(0);
+    for (int64_t i = beg + grp; i < end; i += G) {
+      const int32_t e = __ldg(csr_idx + i);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, A, E>(TF + (int64_t)e * ldt + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) uf[k][j] += x[j];
+          if (DUAL) {
+            vload<A, A, E>(TZ + (int64_t)e * ldt + col, x);
+#pragma unroll
+            for (int j = 0; j < E; ++j) uz[k][j] += x[j];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          uf[k][j] += __shfl_xor_sync(0xffffffffu, uf[k][j], off);
+          if (DUAL) uz[k][j] += __shfl_xor_sync(0xffffffffu, uz[k][j], off);
+        }
+    double d = 0.0;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const int col = (k * LG + l) * E;
+      if (col < cw) {
+        A f[E];
+        vload<A, TX, E>(F + v * ld + c0 + col, f);
+        if (DUAL) {
+          A z[E];
+          vload<A, TX, E>(Zb + v * ld + c0 + col, z);
+#pragma unroll
+          for (int j = 0; j < E; ++j) d += 0.5 * ((double)f[j] * (double)uz[k][j] + (double)z[j] * (double)uf[k][j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < E; ++j) d += (double)f[j] * (double)uf[k][j];
+        }
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < LG; off <<= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+    if (lane == 0) {
+      const double sv = s[v];
+      phi[v] = (c0 == 0 ? 0.0 : phi[v]) + sv * sv * sv * d;
+    }
+  }
+}
+
+// grad_e = -(ex_e / de_e - sum_{v in e} phi_v) + 2 mu w_e   (phi omitted when dv is frozen)
+__global__ void k_grad_final(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
+                             const int32_t* __restrict__ de, const double* __restrict__ ex,
+                             const double* __restrict__ phi, const double* __restrict__ w, double mu,
+                             double* __restrict__ grad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = warp; e < m; e += nwarps) {
+    double acc = 0.0;
+    if (phi)
+      for (int64_t i = csc_ptr[e] + lane, end = csc_ptr[e + 1]; i < end; i += 32) acc += phi[csc_idx[i]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) grad[e] = -(ex[e] / (double)de[e] - acc) + 2.0 * mu * w[e];
+  }
+}
+
+template <class TX, bool DUAL>
+hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld, int c, double mu, bool frozen,
+                             const double* w, double* grad, cudaStream_t st) {
+  using A = typename AccOf<TX>::type;
+  constexpr int E = 16 / (int)sizeof(TX);
+  const int nvec = (c + E - 1) / E;
+  int chunk_vec = std::min(nvec, 128);
+  int lg = 1, nv = 1;
+  pick_tile(chunk_vec, &lg, &nv);
+  const int cc = lg * nv * E;
+  hgl_status stt = HGL_OK;
+  A* TF = static_cast<A*>(buffer_get(g->scratch, sizeof(A) * (size_t)g->m * cc, &stt));
+  if (!TF) return stt;
+  A* TZ = nullptr;
+  if (DUAL) {
+    TZ = static_cast<A*>(buffer_get(g->scratch2, sizeof(A) * (size_t)g->m * cc, &stt));
+    if (!TZ) return stt;
+  }
+  double* vecs = static_cast<double*>(buffer_get(g->misc, sizeof(double) * (size_t)(g->m + g->n + 2), &stt));
+  if (!vecs) return stt;
+  double* ex = vecs;
+  double* phi = vecs + g->m;
+  const int64_t cap = (int64_t)g->num_sms * 8;
+  const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + OP_WARPS - 1) / OP_WARPS, cap));
+  const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + OP_WARPS - 1) / OP_WARPS, cap));
+  for (int c0 = 0; c0 < c; c0 += cc) {
+    const int cw = std::min(cc, c - c0);
+#define HGL_GE(LG_, NV_)                                                                                        \
+  else if (lg == LG_ && nv == NV_) k_grad_edge<TX, LG_, NV_, DUAL><<<grid1, OP_THREADS, 0, st>>>(                 \
+      g->m, g->csc_ptr, g->csc_idx, g->s, g->t, F, Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);
+#define HGL_GV(LG_, NV_)                                                                                        \
+  else if (lg == LG_ && nv == NV_) k_grad_vertex<TX, LG_, NV_, DUAL><<<grid2, OP_THREADS, 0, st>>>(               \
+      g->n, g->csr_ptr, g->csr_idx, g->s, TF, TZ, (int64_t)cc, F, Zb, ld, c0, cw, phi);
+    if (false) {
+    }
+    HGL_FOR_EACH_TILE(HGL_GE)
+    if (!frozen) {
+      if (false) {
+      }
+      HGL_FOR_EACH_TILE(HGL_GV)
+    }
+#undef HGL_GE
+#undef HGL_GV
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
+  k_grad_final<<<grid1, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->de, ex, frozen ? nullptr : phi, w, mu,
+                                             grad);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+// ---- simplex projection (Michelot's support-shrinking iteration) -----------------
+
+struct ProjState {
+  double tau;
+  double prev_count;
+  int32_t done;
+  unsigned counter;
+};
+
+constexpr int PROJ_THREADS = 256;
+
+__global__ void k_proj_init(double* __restrict__ v, const double* __restrict__ w, const double* __restrict__ grad,
+                            double eta, int64_t m, double* __restrict__ part_sum) {
+  __shared__ double red[PROJ_THREADS / 32];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[e] - (grad ? eta * grad[e] : 0.0);
+    v[e] = x;
+    acc += x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < PROJ_THREADS / 32; ++i) s += red[i];
+    part_sum[blockIdx.x] = s;
+  }
+}
+
+// tau_0 = (sum v - 1) / m
+__global__ void k_proj_tau0(const double* __restrict__ part_sum, int nparts, int64_t m, ProjState* ps) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += part_sum[i];
+    ps->tau = (s - 1.0) / (double)m;
+    ps->prev_count = (double)m;
+    ps->done = 0;
+    ps->counter = 0u;
+  }
+}
+
+// One Michelot step: S = {e : v_e > tau}; if |S| unchanged, done; else tau = (sum_S v - 1)/|S|.
+__global__ void k_proj_step(const double* __restrict__ v, int64_t m, double* __restrict__ part_sum,
+                            double* __restrict__ part_cnt, ProjState* ps) {
+  if (((volatile ProjState*)ps)->done) return;
+  __shared__ double rs[PROJ_THREADS / 32], rc[PROJ_THREADS / 32];
+  __shared__ bool last;
+  const double tau = ps->tau;
+  double s = 0.0, cnt = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[e];
+    if (x > tau) {
+      s += x;
+      cnt += 1.0;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rs[threadIdx.x >> 5] = s;
+    rc[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < PROJ_THREADS / 32; ++i) {
+      a += rs[i];
+      b += rc[i];
+    }
+    part_sum[blockIdx.x] = a;
+    part_cnt[blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(&ps->counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+      a += ((volatile double*)part_sum)[i];
+      b += ((volatile double*)part_cnt)[i];
+    }
+    if (b == ps->prev_count || b <= 0.0) {
+      ps->done = 1;
+    } else {
+      ps->tau = (a - 1.0) / b;
+      ps->prev_count = b;
+    }
+    ps->counter = 0u;
+  }
+}
+
+__global__ void k_proj_apply(const double* __restrict__ v, int64_t m, const ProjState* ps, double* __restrict__ w) {
+  const double tau = ps->tau;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[e] - tau;
+    w[e] = x > 0.0 ? x : 0.0;
+  }
+}
+
+}  // namespace
+
+hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
+                              int dtype, double mu, int flags, double* grad, cudaStream_t st) {
+  const bool frozen = (flags & HGL_GRAD_DV_FROZEN) != 0;
+  if (dtype == HGL_FP64) {
+    if (Zb)
+      return grad_launch_typed<double, true>(g, (const double*)F, (const double*)Zb, ld, c, mu, frozen, w, grad, st);
+    return grad_launch_typed<double, false>(g, (const double*)F, nullptr, ld, c, mu, frozen, w, grad, st);
+  }
+  if (dtype == HGL_FP32) {
+    if (Zb)
+      return grad_launch_typed<float, true>(g, (const float*)F, (const float*)Zb, ld, c, mu, frozen, w, grad, st);
+    return grad_launch_typed<float, false>(g, (const float*)F, nullptr, ld, c, mu, frozen, w, grad, st);
+  }
+  return record_error(HGL_ERR_INVALID_ARG, "gradient panels must be FP64 or FP32");
+}
+
+hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
+                          cudaStream_t st, int max_steps) {
+  // work layout: v[m] | part_sum[blocks] | part_cnt[blocks] | ProjState
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
+  double* v = work;
+  double* ps_sum = v + m;
+  double* ps_cnt = ps_sum + blocks;
+  ProjState* ps = reinterpret_cast<ProjState*>(ps_cnt + blocks);
+  k_proj_init<<<blocks, PROJ_THREADS, 0, st>>>(v, w, grad, eta, m, ps_sum);
+  k_proj_tau0<<<1, 32, 0, st>>>(ps_sum, blocks, m, ps);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  int steps = 0;
+  for (;;) {
+    const int batch = 16;
+    for (int k = 0; k < batch; ++k) k_proj_step<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps_sum, ps_cnt, ps);
+    HGL_CHECK_CUDA(cudaGetLastError());
+    steps += batch;
+    if (max_steps > 0 && steps >= max_steps) break;
+    int32_t done = 0;
+    HGL_CHECK_CUDA(cudaMemcpyAsync(&done, &ps->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+    if (done || steps > m + 16) break;
+  }
+  k_proj_apply<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps, w);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+size_t project_work_doubles(int64_t m, int sms) {
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
+  return (size_t)(m + 2 * blocks + 4);
+}
+
+}  // namespace hgl
+
+extern "C" hgl_status hgl_weight_grad(const hgl_graph* g, const double* w, const void* F, const void* Z, int64_t ld,
+                                      int32_t c, hgl_dtype dtype, double mu, int32_t flags, double* grad,
+                                      void* stream) {
+  if (!g || !w || !grad) return hgl::record_error(HGL_ERR_INVALID_ARG, "NULL argument");
+  if (c < 1) return hgl::record_error(HGL_ERR_INVALID_ARG, "c must be >= 1");
+  if (dtype != HGL_FP64 && dtype != HGL_FP32)
+    return hgl::record_error(HGL_ERR_INVALID_ARG, "gradient panels must be FP64 or FP32");
+  HGL_TRY(hgl::check_panel(F, ld, c, hgl::dtype_size(dtype), "F"));
+  if (Z) HGL_TRY(hgl::check_panel(Z, ld, c, hgl::dtype_size(dtype), "Z"));
+  cudaStream_t st = hgl::as_stream(stream);
+  hgl_graph* gg = const_cast<hgl_graph*>(g);
+  HGL_TRY(hgl::degrees_launch(gg, w, st));
+  return hgl::weight_grad_launch(gg, w, F, Z, ld, c, dtype, mu, flags, grad, st);
+}
+
+extern "C" hgl_status hgl_project_simplex(double* w, const double* grad, double eta, int64_t m, void* stream) {
+  if (!w || m < 1) return hgl::record_error(HGL_ERR_INVALID_ARG, "w is NULL or m < 1");
+  cudaStream_t st = hgl::as_stream(stream);
+  const int sms = hgl::device_sm_count();
+  double* work = nullptr;
+  HGL_CHECK_CUDA(cudaMallocAsync(&work, sizeof(double) * hgl::project_work_doubles(m, sms), st));
+  hgl_status s = hgl::project_launch(w, grad, eta, m, work, sms, st, 0);
+  cudaFreeAsync(work, st);
+  return s;
+}
