@@ -133,6 +133,31 @@ hgl_status hgl_apply_theta(const hgl_graph* g, const double* w, double a, double
                            const void* X, int64_t ldx, void* Z, int64_t ldz, int32_t c,
                            hgl_dtype dtype, void* stream);
 
+/*
+ * hgl_apply_theta_noalloc -- the same operator apply as hgl_apply_theta (same
+ * arguments, same result up to the summation order of a narrower column chunk),
+ * but the call allocates no device memory.  The paper has no counterpart: this entry
+ * point serves callers that cannot let a library allocate during the call, such as
+ * programs that route all device memory through their own pool or fixed budget, and
+ * loops that cannot take the implicit synchronisation of cudaMalloc/cudaFree.
+ * hgl_apply_theta allocates its m x chunk intermediate panel on first use; this
+ * variant uses instead a 32 MiB array compiled into the library's device image
+ * (every GPU that loads libhgl holds it until the process exits), narrowing the
+ * column chunk to fit.  Limit: m <= 2,097,152 for FP64 and FP32 panels and
+ * m <= 1,048,576 for BF16 panels, else HGL_ERR_INVALID_ARG (nothing launched).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that first
+ * call before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; it needs no clearing, since the hyperedge pass writes every
+ * entry that the vertex pass then reads.  Calls that overlap on the GPU (on
+ * different streams, or from different host threads) race on the array and give
+ * wrong results: order them.  The graph handle's degree vectors are allocated when
+ * the graph is built, so they are not allocated here either.  Asynchronous.
+ */
+hgl_status hgl_apply_theta_noalloc(const hgl_graph* g, const double* w, double a, double b,
+                                   const void* X, int64_t ldx, void* Z, int64_t ldz,
+                                   int32_t c, hgl_dtype dtype, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Solve (Eq. 6 by conjugate gradient, Eqs. 16-20)                           */
 /* ------------------------------------------------------------------------- */

@@ -105,6 +105,8 @@ struct OpCall {
   double* partials;  // EPI_DOT_XZ / EPI_RESID: [grid2 x c] FP64 partial sums (row stride c)
   const int32_t* run_flag;  // optional device flag: kernels return at once when *run_flag == 0
   int chunk_cols;   // 0 = default column chunk
+  void* scratch;        // optional caller-provided intermediate panel (nullptr = graph-owned buffer)
+  size_t scratch_bytes; // its capacity; the column chunk is narrowed to fit
 };
 
 // Launch both passes of the operator over all column chunks.  Returns the number of

@@ -28,11 +28,24 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   int chunk_vec = cl.chunk_cols > 0 ? (cl.chunk_cols + E - 1) / E : default_chunk_vecs();
   if (chunk_vec > nvec) chunk_vec = nvec;
   if (chunk_vec < 1) chunk_vec = 1;
+  if (cl.scratch) {
+    // narrow the chunk to the largest tile whose m x chunk panel fits the given scratch
+    const size_t per_vec = (size_t)g->m * E * sizeof(TT);
+    const size_t cap = per_vec ? cl.scratch_bytes / per_vec : 0;
+    if (cap < 1)
+      return record_error(HGL_ERR_INVALID_ARG, "m = %lld is too large for the %zu-byte scratch",
+                          (long long)g->m, cl.scratch_bytes);
+    int fit = cap >= 128 ? 128 : (cap >= 64 ? 64 : 1);
+    if (cap < 64)
+      while (fit * 2 <= (int)cap && fit < 32) fit *= 2;
+    if (chunk_vec > fit) chunk_vec = fit;
+  }
   int lg = 1, nv = 1;
   pick_tile(chunk_vec, &lg, &nv);
   const int cc = lg * nv * E;
   hgl_status stt = HGL_OK;
-  TT* Tp = static_cast<TT*>(buffer_get(g->scratch, sizeof(TT) * (size_t)g->m * (size_t)cc, &stt));
+  TT* Tp = cl.scratch ? static_cast<TT*>(cl.scratch)
+                      : static_cast<TT*>(buffer_get(g->scratch, sizeof(TT) * (size_t)g->m * (size_t)cc, &stt));
   if (!Tp) return stt;
   const int grid1 = edge_grid(g), grid2 = vertex_grid(g);
   const TX* X = static_cast<const TX*>(cl.X);

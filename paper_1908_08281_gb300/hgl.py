@@ -74,6 +74,7 @@ _SIGNATURES = {
     "hgl_graph_export": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "hgl_degrees": (_I32, [_P, _P, _P, _P, _P, _P]),
     "hgl_apply_theta": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
+    "hgl_apply_theta_noalloc": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P, _P,
                             ctypes.POINTER(SolveStats), _P]),
     "hgl_block_rsvd": (_I32, [_P, _P, _D, ctypes.POINTER(_I64), _I32, _I32, _I32, _I32, _U64, _I32, _P,
@@ -252,6 +253,18 @@ def apply_theta(g: Graph, w: torch.Tensor, X: torch.Tensor, a: float = 0.0, b: f
     if dt != dtz:
         raise ValueError("X and Z must have the same dtype")
     _check(lib().hgl_apply_theta(g.handle, _vec(w, "w"), a, b, px, ldx, pz, ldz, c, dt, _stream(stream)))
+    return Z
+
+
+def apply_theta_noalloc(g: Graph, w: torch.Tensor, X: torch.Tensor, Z: torch.Tensor, a: float = 0.0,
+                        b: float = 1.0, stream=None) -> torch.Tensor:
+    """Z = a X + b Theta(w) X without any device allocation in the call (Z is required)."""
+    n, c = X.shape
+    px, ldx, dt = _panel(X, "X")
+    pz, ldz, dtz = _panel(Z, "Z")
+    if dt != dtz:
+        raise ValueError("X and Z must have the same dtype")
+    _check(lib().hgl_apply_theta_noalloc(g.handle, _vec(w, "w"), a, b, px, ldx, pz, ldz, c, dt, _stream(stream)))
     return Z
 
 
