@@ -125,6 +125,7 @@ void hgl_graph_destroy(hgl_graph* g) {
   hgl::buffer_free(g->solver);
   hgl::buffer_free(g->misc);
   hgl::buffer_free(g->step);
+  hgl::buffer_free(g->rsvd);
   delete g;
 }
 

@@ -434,6 +434,15 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   return verdict;
 }
 
+hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            double* partials, cudaStream_t st, int* rows) {
+  if (dt == HGL_FP64)
+    return panel_dot<double, double>(g, c, (const double*)A, lda, (const double*)B, ldb, 1.0, partials, st, rows);
+  if (dt == HGL_FP32)
+    return panel_dot<float, float>(g, c, (const float*)A, lda, (const float*)B, ldb, 1.0, partials, st, rows);
+  return record_error(HGL_ERR_INVALID_ARG, "dot panels must be FP64 or FP32");
+}
+
 hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out) {
   hgl_graph* gg = const_cast<hgl_graph*>(g);
   VecGrid vg = vec_grid(g, c, 8);

@@ -48,6 +48,7 @@ struct hgl_graph {
   hgl::Buffer solver;          // CG panels and per-column state
   hgl::Buffer misc;            // gradient vectors (ex[m], phi[n])
   hgl::Buffer step;            // adaptive-step vectors (grad, w_old, projection work)
+  hgl::Buffer rsvd;            // block rSVD work space (dense blocks, bases, Grams)
   int chunk_cols = 0;          // operator column chunk (0 = library default)
 };
 
@@ -57,10 +58,10 @@ struct hgl_graph {
     if (e_ != cudaSuccess) return ::hgl::cuda_error(e_, #call, __FILE__, __LINE__); \
   } while (0)
 
-#define HGL_TRY(expr)                      \
-  do {                                     \
-    hgl_status s_ = (expr);                \
-    if (s_ != HGL_OK) return s_;           \
+#define HGL_TRY(expr)                                      \
+  do {                                                     \
+    hgl_status hgl_try_status_ = (expr);                   \
+    if (hgl_try_status_ != HGL_OK) return hgl_try_status_; \
   } while (0)
 
 namespace hgl {

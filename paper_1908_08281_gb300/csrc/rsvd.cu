@@ -1,0 +1,412 @@
+// rsvd.cu -- hgl_block_rsvd and the block preconditioner (Section 3, Algorithm 1 and
+// Eq. 15).
+//
+// For every diagonal tessellation block b (contiguous vertex range) the dense block
+// Theta_bb is assembled, and Algorithm 1 runs on it with l = k + p columns:
+//   Y0 = Theta_bb Omega, S0 = QR(Y0);  q times: S~ = QR(Theta_bb S), S = QR(Theta_bb S~)
+// (Theta_bb is symmetric, so the transposed products of Algorithm 1 are plain products),
+// then T = S^T Theta_bb S (Rayleigh-Ritz, in place of the SVD of S^T X), T = V diag(ev) V^T,
+// and Q_b = S V (top k).  Every QR is CholeskyQR2: G = Y^T Y, G = L L^T, Q = Y L^-T, twice.
+// All blocks go through each step together: one grouped GEMM launch per product
+// (tcgen05 tensor cores with BF16 operands, or FP64 CUDA cores for checking), one Gram,
+// one Cholesky and one triangular-apply launch per orthonormalisation.
+//
+// The preconditioner applies z_b = r_b/(1+lam) + Q_b diag(g_b) Q_b^T r_b with
+// g = ev / ((1+lam)(1+lam-ev)): the exact inverse of M_bb = (1+lam) I - Theta_bb on the
+// span of Q_b, and 1/(1+lam) on its complement.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "rsvd_kernels.cuh"
+#include "precond.cuh"
+#include "solver.cuh"
+#include "umma.cuh"
+
+namespace hgl {
+namespace {
+
+constexpr int MAX_L = 96;
+
+inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+hgl_status get_encoder(EncodeTiledFn* out) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      return record_error(HGL_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *out = fn;
+  return HGL_OK;
+}
+
+// 2-D BF16 tensor map, 128-byte swizzle, box of 64 elements x box_rows rows.
+hgl_status make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                    uint32_t box_rows) {
+  EncodeTiledFn enc = nullptr;
+  HGL_TRY(get_encoder(&enc));
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {64u, box_rows};
+  cuuint32_t es[2] = {1u, 1u};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return record_error(HGL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return HGL_OK;
+}
+
+#define HGL_LPAD_SWITCH(lp, ...)                              \
+  switch (lp) {                                               \
+    case 16: { constexpr int LP = 16; __VA_ARGS__; } break;   \
+    case 32: { constexpr int LP = 32; __VA_ARGS__; } break;   \
+    case 48: { constexpr int LP = 48; __VA_ARGS__; } break;   \
+    case 64: { constexpr int LP = 64; __VA_ARGS__; } break;   \
+    case 80: { constexpr int LP = 80; __VA_ARGS__; } break;   \
+    default: { constexpr int LP = 96; __VA_ARGS__; } break;   \
+  }
+
+struct Work {
+  // host metadata
+  std::vector<int64_t> v0, arow, koff;
+  std::vector<int32_t> rows, lb, kb, unit_block, unit_tile;
+  int64_t rows_tot = 0, Ktot = 0, ldA = 0;
+  // device pointers (inside g->rsvd)
+  rsvd::Blocks B{};
+  int32_t* d_unit_block = nullptr;
+  int32_t* d_unit_tile = nullptr;
+  void* A = nullptr;      // rows_tot x ldA (BF16 or FP64)
+  void* St = nullptr;     // lpad x Ktot (BF16 or FP64)
+  void* D = nullptr;      // rows_tot x lpad (FP32 or FP64)
+  void* Qf = nullptr;     // rows_tot x lpad (FP32 or FP64)
+  double* G = nullptr;    // nb x lpad x lpad
+  double* R = nullptr;    // nb x lpad x lpad
+  double* ev = nullptr;   // nb x lpad
+  int32_t* fail = nullptr;
+  int* err = nullptr;
+};
+
+inline size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
+
+hgl_status plan(hgl_graph* g, const int64_t* bp, int nb, int k, int l, int lpad, int dtype, Work* w) {
+  const bool bf16 = dtype == HGL_BF16;
+  w->v0.resize(nb);
+  w->arow.resize(nb);
+  w->koff.resize(nb);
+  w->rows.resize(nb);
+  w->lb.resize(nb);
+  w->kb.resize(nb);
+  int64_t maxb = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t sz = bp[b + 1] - bp[b];
+    w->v0[b] = bp[b];
+    w->rows[b] = (int32_t)sz;
+    w->arow[b] = w->rows_tot;
+    w->koff[b] = w->Ktot;
+    w->rows_tot += rup(sz, 128);
+    w->Ktot += rup(sz, 64);
+    w->lb[b] = (int32_t)std::min<int64_t>(l, sz);
+    w->kb[b] = (int32_t)std::min<int64_t>(k, sz);
+    maxb = std::max(maxb, sz);
+  }
+  w->ldA = rup(maxb, 64);
+  // units: 128-row tiles, blocks ordered by decreasing size (balances the persistent GEMM)
+  std::vector<int> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w->rows[a] > w->rows[b]; });
+  for (int b : order)
+    for (int t = 0; t < (w->rows[b] + 127) / 128; ++t) {
+      w->unit_block.push_back(b);
+      w->unit_tile.push_back(t);
+    }
+  const size_t ea = bf16 ? 2 : 8, ed = bf16 ? 4 : 8;
+  const size_t nu = w->unit_block.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += a256(bytes);
+    return o;
+  };
+  const size_t oA = take(ea * (size_t)w->rows_tot * (size_t)w->ldA);
+  const size_t oSt = take(ea * (size_t)lpad * (size_t)w->Ktot);
+  const size_t oD = take(ed * (size_t)w->rows_tot * lpad);
+  const size_t oQf = take(ed * (size_t)w->rows_tot * lpad);
+  const size_t oG = take(8 * (size_t)nb * lpad * lpad);
+  const size_t oR = take(8 * (size_t)nb * lpad * lpad);
+  const size_t oEv = take(8 * (size_t)nb * lpad);
+  const size_t oMeta = take(8 * 3 * (size_t)nb + 4 * 3 * (size_t)nb + 4 * 2 * nu + 64);
+  hgl_status st = HGL_OK;
+  char* base = static_cast<char*>(buffer_get(g->rsvd, off, &st));
+  if (!base) return st;
+  w->A = base + oA;
+  w->St = base + oSt;
+  w->D = base + oD;
+  w->Qf = base + oQf;
+  w->G = reinterpret_cast<double*>(base + oG);
+  w->R = reinterpret_cast<double*>(base + oR);
+  w->ev = reinterpret_cast<double*>(base + oEv);
+  char* meta = base + oMeta;
+  int64_t* d_v0 = reinterpret_cast<int64_t*>(meta);
+  int64_t* d_arow = d_v0 + nb;
+  int64_t* d_koff = d_arow + nb;
+  int32_t* d_rows = reinterpret_cast<int32_t*>(d_koff + nb);
+  int32_t* d_lb = d_rows + nb;
+  int32_t* d_kb = d_lb + nb;
+  w->d_unit_block = d_kb + nb;
+  w->d_unit_tile = w->d_unit_block + nu;
+  w->fail = w->d_unit_tile + nu;
+  w->err = w->fail + 1;
+  // one host staging buffer, one copy
+  std::vector<char> hmeta(8 * 3 * (size_t)nb + 4 * 3 * (size_t)nb + 4 * 2 * nu + 8, 0);
+  char* h = hmeta.data();
+  memcpy(h, w->v0.data(), 8 * nb);
+  memcpy(h + 8 * nb, w->arow.data(), 8 * nb);
+  memcpy(h + 16 * nb, w->koff.data(), 8 * nb);
+  memcpy(h + 24 * nb, w->rows.data(), 4 * nb);
+  memcpy(h + 28 * nb, w->lb.data(), 4 * nb);
+  memcpy(h + 32 * nb, w->kb.data(), 4 * nb);
+  memcpy(h + 36 * nb, w->unit_block.data(), 4 * nu);
+  memcpy(h + 36 * nb + 4 * nu, w->unit_tile.data(), 4 * nu);
+  HGL_CHECK_CUDA(cudaMemcpy(meta, hmeta.data(), hmeta.size(), cudaMemcpyHostToDevice));
+  rsvd::Blocks& B = w->B;
+  B.nb = nb;
+  B.l = l;
+  B.lpad = lpad;
+  B.k = k;
+  B.ldA = w->ldA;
+  B.Ktot = w->Ktot;
+  B.v0 = d_v0;
+  B.rows = d_rows;
+  B.arow = d_arow;
+  B.koff = d_koff;
+  B.lb = d_lb;
+  B.kb = d_kb;
+  return HGL_OK;
+}
+
+template <class F>
+hgl_status set_smem(F* fn, size_t bytes) {
+  HGL_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)bytes));
+  return HGL_OK;
+}
+
+// D = Theta_bb * S for all blocks (St holds S^T).
+template <int LP>
+hgl_status gemm(const Work& w, int dtype, int sms, cudaStream_t st) {
+  const int nu = (int)w.unit_block.size();
+  if (dtype == HGL_BF16) {
+    CUtensorMap ma, mb;
+    HGL_TRY(make_map(&ma, w.A, (uint64_t)w.ldA, (uint64_t)w.rows_tot, (uint64_t)w.ldA * 2, 128));
+    HGL_TRY(make_map(&mb, w.St, (uint64_t)w.Ktot, (uint64_t)LP, (uint64_t)w.Ktot * 2, LP));
+    umma::GemmUnits U{w.d_unit_block, w.d_unit_tile, w.B.rows, w.B.arow, w.B.koff, nu};
+    const size_t smem = umma::gemm_smem_bytes(LP);
+    HGL_TRY(set_smem(umma::k_block_gemm<LP>, smem));
+    const int grid = std::min(nu, sms);
+    umma::k_block_gemm<LP><<<grid, umma::THREADS, smem, st>>>(ma, mb, U, static_cast<float*>(w.D), LP, w.err);
+  } else {
+    const int grid = std::min(nu, sms * 4);
+    rsvd::k_block_gemm_f64<LP><<<grid, 256, 0, st>>>(w.B, w.d_unit_block, w.d_unit_tile, nu,
+                                                      static_cast<const double*>(w.A),
+                                                      static_cast<const double*>(w.St), static_cast<double*>(w.D));
+  }
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+// Q = CholeskyQR2(D): G = D^T D, Rinv = chol^-T, Qf = D Rinv; again on Qf.  The final
+// pass also refreshes the transposed basis St (when write_st).
+template <class T, class TB, int LP>
+hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool write_st) {
+  const int nb = w.B.nb;
+  const int nu = (int)w.unit_block.size();
+  const size_t chol_smem = 2 * sizeof(double) * LP * LP;
+  HGL_TRY(set_smem(rsvd::k_chol_inv<LP>, chol_smem));
+  const size_t ap_smem = sizeof(T) * (LP * LP + 32 * LP);
+  HGL_TRY(set_smem(rsvd::k_apply_rinv<T, TB, LP>, ap_smem));
+  const double shift = dtype == HGL_BF16 ? 1e-6 : 1e-14;
+  const T* Y = static_cast<const T*>(w.D);
+  T* Qf = static_cast<T*>(w.Qf);
+  for (int pass = 0; pass < 2; ++pass) {
+    rsvd::k_gram<T, LP><<<nb, 256, 0, st>>>(w.B, Y, Y, w.G);
+    rsvd::k_chol_inv<LP><<<nb, 256, chol_smem, st>>>(w.B, w.G, pass == 0 ? shift : 0.0, w.R, w.fail);
+    const bool last = pass == 1;
+    // in-place on the second pass is fine: each tile reads its rows before writing them
+    rsvd::k_apply_rinv<T, TB, LP><<<std::min(nu, sms * 4), 256, ap_smem, st>>>(
+        w.B, w.d_unit_block, w.d_unit_tile, nu, Y, w.R, Qf, (last && write_st) ? static_cast<TB*>(w.St) : nullptr);
+    HGL_CHECK_CUDA(cudaGetLastError());
+    Y = Qf;
+  }
+  return HGL_OK;
+}
+
+}  // namespace
+
+hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const int64_t* bp, int32_t nb, int32_t k,
+                         int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st, hgl_precond** out,
+                         bool degrees_ready) {
+  hgl_graph* g = const_cast<hgl_graph*>(gc);
+  *out = nullptr;
+  if (!bp || nb < 1) return record_error(HGL_ERR_INVALID_ARG, "block_ptr is NULL or nblocks < 1");
+  if (k < 1 || p < 0 || q < 0 || k + p > MAX_L)
+    return record_error(HGL_ERR_INVALID_ARG, "need k >= 1, p >= 0, q >= 0 and k + p <= %d", MAX_L);
+  if (gemm_dtype != HGL_BF16 && gemm_dtype != HGL_FP64)
+    return record_error(HGL_ERR_INVALID_ARG, "gemm_dtype must be HGL_BF16 or HGL_FP64");
+  if (bp[0] != 0 || bp[nb] != g->n) return record_error(HGL_ERR_INVALID_ARG, "block_ptr must run from 0 to n");
+  for (int b = 0; b < nb; ++b)
+    if (bp[b + 1] <= bp[b]) return record_error(HGL_ERR_INVALID_ARG, "blocks must be non-empty and increasing");
+  const int l = k + p;
+  const int lpad = (int)rup(l, 16);
+  const int sms = g->num_sms;
+  if (!degrees_ready) HGL_TRY(degrees_launch(g, w, st));
+
+  Work wk;
+  HGL_TRY(plan(g, bp, nb, k, l, lpad, gemm_dtype, &wk));
+  HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
+  const bool bf16 = gemm_dtype == HGL_BF16;
+
+  // dense diagonal blocks and the Gaussian start basis
+  if (bf16) {
+    rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                            g->csc_idx, g->s, g->t,
+                                                            static_cast<__nv_bfloat16*>(wk.A));
+    rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<__nv_bfloat16*>(wk.St));
+  } else {
+    rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                     g->csc_idx, g->s, g->t, static_cast<double*>(wk.A));
+    rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<double*>(wk.St));
+  }
+  HGL_CHECK_CUDA(cudaGetLastError());
+
+  // Algorithm 1: 1 + 2q products each followed by an orthonormalisation, then W = Theta S
+  const int nprod = 1 + 2 * q;
+  hgl_status s_ = HGL_OK;
+  HGL_LPAD_SWITCH(lpad, {
+    for (int i = 0; i < nprod && s_ == HGL_OK; ++i) {
+      s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+      if (s_ == HGL_OK)
+        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, true)
+                  : cholqr2<double, double, LP>(wk, gemm_dtype, sms, st, true);
+    }
+    if (s_ == HGL_OK) s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+    if (s_ == HGL_OK) {
+      // T = S^T (Theta S), eigendecomposition, Ritz vectors
+      if (bf16)
+        rsvd::k_gram<float, LP><<<nb, 256, 0, st>>>(wk.B, static_cast<const float*>(wk.Qf),
+                                                   static_cast<const float*>(wk.D), wk.G);
+      else
+        rsvd::k_gram<double, LP><<<nb, 256, 0, st>>>(wk.B, static_cast<const double*>(wk.Qf),
+                                                    static_cast<const double*>(wk.D), wk.G);
+      const size_t jsm = 2 * sizeof(double) * LP * LP;
+      s_ = set_smem(rsvd::k_jacobi<LP>, jsm);
+      if (s_ == HGL_OK) rsvd::k_jacobi<LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40);
+    }
+  });
+  HGL_TRY(s_);
+  HGL_CHECK_CUDA(cudaGetLastError());
+
+  // the handle: Q (n x k), gains, eigenvalues, block metadata and 32-row apply tiles
+  hgl_precond* P = new (std::nothrow) hgl_precond();
+  if (!P) return record_error(HGL_ERR_OOM, "host allocation failed");
+  P->g = g;
+  P->n = g->n;
+  P->nb = nb;
+  P->k = k;
+  P->l = l;
+  P->lpad = lpad;
+  P->lam = lam;
+  P->dtype = gemm_dtype;
+  P->bptr.assign(bp, bp + nb + 1);
+  P->kb = wk.kb;
+  std::vector<int32_t> ub, ut;
+  for (int b = 0; b < nb; ++b)
+    for (int t = 0; t < (wk.rows[b] + 31) / 32; ++t) {
+      ub.push_back(b);
+      ut.push_back(t);
+    }
+  P->nunits = (int)ub.size();
+  const size_t eq = bf16 ? 4 : 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += a256(bytes);
+    return o;
+  };
+  const size_t oQ = take(eq * (size_t)g->n * k);
+  const size_t oGain = take(8 * (size_t)nb * k);
+  const size_t oEv = take(8 * (size_t)nb * k);
+  const size_t oV0 = take(8 * (size_t)(nb + 1));
+  const size_t oRows = take(4 * (size_t)nb);
+  const size_t oKb = take(4 * (size_t)nb);
+  const size_t oUb = take(4 * ub.size());
+  const size_t oUt = take(4 * ut.size());
+  cudaError_t e = cudaMalloc(&P->dev, off);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_error(e, "cudaMalloc(preconditioner)", __FILE__, __LINE__);
+  }
+  char* base = static_cast<char*>(P->dev);
+  P->Q = base + oQ;
+  P->gain = reinterpret_cast<double*>(base + oGain);
+  P->ev = reinterpret_cast<double*>(base + oEv);
+  P->d_v0 = reinterpret_cast<int64_t*>(base + oV0);
+  P->d_rows = reinterpret_cast<int32_t*>(base + oRows);
+  P->d_kb = reinterpret_cast<int32_t*>(base + oKb);
+  P->unit_block = reinterpret_cast<int32_t*>(base + oUb);
+  P->unit_tile = reinterpret_cast<int32_t*>(base + oUt);
+  hgl_status fin = HGL_OK;
+  auto chk = [&](cudaError_t ce) {
+    if (ce != cudaSuccess && fin == HGL_OK) fin = cuda_error(ce, "preconditioner setup", __FILE__, __LINE__);
+  };
+  chk(cudaMemcpyAsync(P->d_v0, bp, 8 * (size_t)(nb + 1), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->d_rows, wk.rows.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->d_kb, wk.kb.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->unit_block, ub.data(), 4 * ub.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->unit_tile, ut.data(), 4 * ut.size(), cudaMemcpyHostToDevice, st));
+  const int nu = (int)wk.unit_block.size();
+  if (fin == HGL_OK) {
+    HGL_LPAD_SWITCH(lpad, {
+      if (bf16) {
+        const size_t rs = sizeof(float) * LP * k;
+        fin = set_smem(rsvd::k_ritz<float, LP>, rs);
+        if (fin == HGL_OK)
+          rsvd::k_ritz<float, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
+              wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const float*>(wk.Qf), wk.R,
+              static_cast<float*>(P->Q));
+      } else {
+        const size_t rs = sizeof(double) * LP * k;
+        fin = set_smem(rsvd::k_ritz<double, LP>, rs);
+        if (fin == HGL_OK)
+          rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
+              wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R,
+              static_cast<double*>(P->Q));
+      }
+    });
+  }
+  if (fin == HGL_OK) fin = precond_gains_launch(P, wk.ev, lpad, st);
+  if (fin == HGL_OK) {
+    int32_t flags[2] = {0, 0};
+    chk(cudaMemcpyAsync(flags, wk.fail, 8, cudaMemcpyDeviceToHost, st));
+    chk(cudaStreamSynchronize(st));
+    if (fin == HGL_OK && flags[1] != 0)
+      fin = record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
+  }
+  if (fin != HGL_OK) {
+    cudaFree(P->dev);
+    delete P;
+    return fin;
+  }
+  *out = P;
+  return HGL_OK;
+}
+
+}  // namespace hgl

@@ -37,6 +37,14 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
 
 int cg_iteration_bound(double lam, double tol);
 
+// per-column partial sums of A.B for panels of type dt (FP64 or FP32); rows in *rows
+hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,
+                            double* partials, cudaStream_t st, int* rows);
+
+hgl_status precond_build(const hgl_graph* g, const double* w, double lam, const int64_t* block_ptr, int32_t nblocks,
+                         int32_t k, int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st,
+                         hgl_precond** out, bool degrees_ready);
+
 // sum over all entries of F*F (FP64 panel), deterministic; synchronises the stream.
 hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out);
 

@@ -14,9 +14,6 @@ hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, cons
 hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
                           cudaStream_t st, int max_steps);
 size_t project_work_doubles(int64_t m, int sms);
-hgl_status precond_build(const hgl_graph* g, const double* w, double lam, const int64_t* block_ptr, int32_t nblocks,
-                         int32_t k, int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st,
-                         hgl_precond** out, bool degrees_ready);
 
 namespace {
 

@@ -1,0 +1,157 @@
+"""GPU parity of the block randomized SVD (Algorithm 1) and the block preconditioner:
+FP64 path against the oracle's Rayleigh-Ritz rSVD with the same Philox Omega, BF16
+tensor-core path against the FP64 path, and preconditioned CG against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import core, incidence, rsvd
+from paper_1908_08281_gb300 import build as _build
+from paper_1908_08281_gb300 import hgl
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available()
+    _build.build()
+    hgl.lib()
+
+
+def _setup(n=1500, m=2500, c=4, seed=0, wseed=1):
+    wl = synth.WORKLOADS["batched_rsvd"]
+    d = synth.make_hypergraph(wl, seed, n=n, m=m, c=c)
+    og = incidence.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    H = incidence.incidence_matrix(og)
+    rng = np.random.default_rng(wseed)
+    w = rng.random(d["m"]) + 0.05
+    w /= w.sum()
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    return wl, d, H, w, g
+
+
+def _panel(a, dtype=torch.float64):
+    P = hgl.padded_panel(a.shape[0], a.shape[1], dtype, DEV)
+    P.copy_(torch.from_numpy(np.ascontiguousarray(a)).to(dtype))
+    return P
+
+
+K, P_, Q_, SEED = 8, 4, 2, 1234
+
+
+def test_rsvd_fp64_matches_oracle():
+    wl, d, H, w, g = _setup()
+    bp = d["block_ptr"]
+    lam = wl.lam
+    Pc = hgl.block_rsvd(g, torch.tensor(w, device=DEV), lam, bp, K, P_, Q_, SEED, gemm_dtype=hgl.HGL_FP64)
+    fac = rsvd.block_rsvd(H, w, bp, K, P_, Q_, SEED)
+    for b in range(len(bp) - 1):
+        Qg, evg = hgl.precond_export(Pc, b)
+        Qo, evo = fac[b]
+        evg = evg.cpu().numpy()
+        assert Qg.shape[1] == len(evo)
+        assert np.allclose(evg, np.clip(evo, 0, 1), rtol=1e-10, atol=1e-12), (b, evg, evo)
+    # the preconditioner itself (invariant under rotations inside eigenspaces)
+    rng = np.random.default_rng(3)
+    R = rng.standard_normal((d["n"], 5))
+    Z = hgl.precond_apply(Pc, _panel(R)).cpu().numpy()
+    Zo = rsvd.precond_apply(fac, bp, lam, R)
+    assert np.allclose(Z, Zo, rtol=1e-9, atol=1e-10 * np.abs(Zo).max())
+    # FP32 panels through the same factors
+    Z32 = hgl.precond_apply(Pc, _panel(R, torch.float32)).to(torch.float64).cpu().numpy()
+    assert np.abs(Z32 - Zo).max() <= 1e-5 * np.abs(Zo).max()
+
+
+@pytest.mark.parametrize("k,p", [(8, 4), (16, 8), (40, 8), (64, 10)])
+def test_rsvd_bf16_tensor_cores_vs_fp64(k, p):
+    wl, d, H, w, g = _setup(n=12000, m=20000, seed=2)
+    bp = d["block_ptr"]
+    wt = torch.tensor(w, device=DEV)
+    P64 = hgl.block_rsvd(g, wt, wl.lam, bp, k, p, Q_, SEED, gemm_dtype=hgl.HGL_FP64)
+    P16 = hgl.block_rsvd(g, wt, wl.lam, bp, k, p, Q_, SEED, gemm_dtype=hgl.HGL_BF16)
+    blocks = rsvd.block_theta(H, w, bp)
+    worst = 0.0
+    for b in range(len(bp) - 1):
+        q64, e64 = hgl.precond_export(P64, b)
+        q16, e16 = hgl.precond_export(P16, b)
+        e64, e16 = e64.cpu().numpy(), e16.cpu().numpy()
+        q64, q16 = q64.cpu().numpy(), q16.cpu().numpy()
+        worst = max(worst, np.abs(e64 - e16).max() / max(e64.max(), 1e-12))
+        # orthonormal Ritz vectors (FP32 CholeskyQR2 on FP32 products)
+        assert np.abs(q16.T @ q16 - np.eye(q16.shape[1])).max() <= 1e-5
+        if b < 8:
+            # Ritz residual against the exact FP64 block: BF16 operands cost ~2^-8 relative
+            Tb = blocks[b]
+            r16 = np.linalg.norm(Tb @ q16 - q16 * e16, axis=0)
+            r64 = np.linalg.norm(Tb @ q64 - q64 * e64, axis=0)
+            assert (r16 <= r64 + 2e-2 * max(e64.max(), 1e-12)).all(), (b, r16.max(), r64.max())
+    # BF16 storage of Theta_bb and of the basis: a few units of 2^-8 in the Ritz values
+    assert worst <= 3e-2, worst
+    rng = np.random.default_rng(4)
+    Rn = rng.standard_normal((d["n"], 7))
+    Z64 = hgl.precond_apply(P64, _panel(Rn)).cpu().numpy()
+    for Pc, dt in ((P16, torch.float64), (P16, torch.float32), (P64, torch.float32)):
+        Z = hgl.precond_apply(Pc, _panel(Rn, dt)).to(torch.float64).cpu().numpy()
+        assert np.isfinite(Z).all()
+        # symmetric positive definite: r^T P^-1 r > 0 for every column
+        assert ((Rn * Z).sum(axis=0) > 0).all()
+        # eigenvectors near the rank cut may trade places between the two factorisations;
+        # the operators still agree in norm
+        assert np.linalg.norm(Z - Z64) <= 3e-2 * np.linalg.norm(Z64)
+
+
+def test_pcg_fp64_reaches_oracle_solution():
+    wl, d, H, w, g = _setup(n=2000, m=3000, c=6, seed=5)
+    bp = d["block_ptr"]
+    wt = torch.tensor(w, device=DEV)
+    Pc = hgl.block_rsvd(g, wt, wl.lam, bp, K, P_, Q_, SEED, gemm_dtype=hgl.HGL_FP64)
+    Y = _panel(d["Y"])
+    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=1e-10, precond=Pc)
+    ref = core.solve_dense(H, w, wl.lam, d["Y"])
+    err = np.linalg.norm(F.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-10
+    fac = rsvd.block_rsvd(H, w, bp, K, P_, Q_, SEED)
+    oc = core.cg_solve(H, w, wl.lam, d["Y"], tol=1e-10, precond=lambda R: rsvd.precond_apply(fac, bp, wl.lam, R))
+    assert np.abs(iters.cpu().numpy() - oc["iters"]).max() <= 1
+
+
+@pytest.mark.parametrize("mode", [hgl.HGL_FP32, hgl.HGL_BF16])
+def test_pcg_mixed_with_tensor_core_preconditioner(mode):
+    wl, d, H, w, g = _setup(n=6000, m=10000, c=16, seed=6)
+    bp = d["block_ptr"]
+    wt = torch.tensor(w, device=DEV)
+    Pc = hgl.block_rsvd(g, wt, wl.lam, bp, 16, 8, 2, SEED, gemm_dtype=hgl.HGL_BF16)
+    Y = _panel(d["Y"])
+    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=1e-8, dtype=mode, precond=Pc)
+    ref, _ = core.certified_solve(H, w, wl.lam, d["Y"])
+    err = np.linalg.norm(F.cpu().numpy() - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-5
+    assert st.relres_max <= 1e-8
+
+
+def test_adaptive_step_br_route_matches_oracle():
+    wl, d, H, w, g = _setup(n=1500, m=2500, c=5, seed=7)
+    bp = d["block_ptr"]
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    for _ in range(2):
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 0.0, 1e-2, tol=1e-10, route=hgl.HGL_ROUTE_BR, block_ptr=bp,
+                               k=K, p=P_, q=Q_, seed=SEED)
+        assert st.solve.relres_max <= 1e-10
+    Fr, wr, _ = core.adaptive_loop(H, d["w0"], wl.lam, 0.0, 1e-2, d["Y"], 2, tol=1e-12)
+    err = np.linalg.norm(F.cpu().numpy() - Fr, axis=0) / np.linalg.norm(Fr, axis=0)
+    assert err.max() <= 1e-9
+    assert np.linalg.norm(wt.cpu().numpy() - wr) / np.linalg.norm(wr) <= 1e-9
+
+
+def test_rsvd_argument_errors():
+    wl, d, H, w, g = _setup(n=600, m=900)
+    wt = torch.tensor(w, device=DEV)
+    for bp, k, p in [([0, 300, 599], 4, 2), ([0, 300, 300, 600], 4, 2), ([0, 600], 90, 10)]:
+        with pytest.raises(hgl.HglError) as ei:
+            hgl.block_rsvd(g, wt, 0.5, bp, k, p, 1, 1)
+        assert ei.value.name == "HGL_ERR_INVALID_ARG"
