@@ -3,11 +3,15 @@
 Workload "full_adaptive": random hypergraph with n = 1,000,000 vertices, m = 2,000,000
 hyperedges, truncated power-law hyperedge sizes on 2..2000 (exponent solved for a mean
 of 10, about 20M incidences), Y n x 512 binary with 0.5% ones, lam = 0.5, w0 = 1/m,
-eta = 1e-2.  A step is one outer iteration of the alternation (solve M F = lam Y at w,
-warm-started from the previous F, to a relative residual that bounds the relative
-error by 1e-5; then the gradient of P(w) and the projected step on w), computed by
-libhgl in mixed precision (FP32 panels, FP64 refinement and reductions).  The plain
-FP64 block CG of the same library is timed on the same GPU as the comparator.
+eta = 1e-2, 20 outer iterations.
+
+A step is one outer iteration of that 20-iteration adaptive loop (the state w, F is
+reset to w0, 0 every 20 steps): the block rSVD preconditioner at the current w
+(diagonal blocks of 1,024-8,192 vertices, k = 64, p = 10, q = 2, BF16 tensor cores),
+the preconditioned CG solve warm-started from the previous F to a relative residual
+that bounds the relative error by 1e-5 (FP32 panels inside FP64-accurate
+refinement), the gradient of P(w) and the projected step on w.  The comparator is the
+plain FP64 block CG of the same library on the same loop on the same GPU.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Prints one JSON line on rank 0.
@@ -34,26 +38,27 @@ METRIC = "adaptive outer iterations/sec (rel err <= 1e-5)"
 UNIT = "iters/s"
 TOL = 3e-6          # relative residual; kappa(M) <= 3 at lam = 0.5 -> relative error <= 9e-6
 SEED = 20190822
+LOOP = 20           # outer iterations of one adaptive loop
+K_RANK, P_OVER, Q_ITERS = 64, 10, 2
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hgl", choices=["hgl", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--scale", type=float, default=1.0, help="shrink n and m (testing only)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--eta", type=float, default=None, help="override the workload's step size")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 class ClockSampler:
@@ -73,8 +78,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
 
@@ -90,18 +94,25 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if len(r) >= 9 and num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if len(r) >= 9 and num(r[2]) is not None]
+        pw = [num(r[3]) for r in self.rows if len(r) >= 9 and num(r[3]) is not None]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in self.rows:
-            if len(r) < 9:
-                continue
-            for nm, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(nm)
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def measured_peaks():
@@ -109,84 +120,130 @@ def measured_peaks():
     if os.path.exists(p):
         with open(p) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1925.6)), "measured"
+    return 6800.0, 1900.0, "fallback"
 
 
 def make_inputs(scale: float):
     wl = synth.WORKLOADS[WORKLOAD]
-    n = int(wl.n * scale)
-    m = int(wl.m * scale)
     t0 = time.time()
-    d = synth.make_hypergraph(wl, SEED, n=n, m=m, tags_dtype=np.float64)
+    d = synth.make_hypergraph(wl, SEED, n=int(wl.n * scale), m=int(wl.m * scale), tags_dtype=np.float64)
     d["gen_s"] = time.time() - t0
     d["wl"] = wl
     return d
 
 
-def theta_algorithmic_bytes(n, m, nnz, c, elt):
-    """Compulsory bytes of one operator apply Z = a X + b Theta X (one column chunk):
-    index arrays once, X read by both passes, the intermediate m x c panel written
-    and read once, Z written once, and the scaling vectors."""
-    index = 2 * 4 * nnz + 8 * (n + 1) + 8 * (m + 1)
-    panels = 2 * n * c * elt + 2 * m * c * 4 + n * c * elt
-    scal = 8 * (2 * n + m)
-    return index + panels + scal
+# ---- algorithmic bytes per launch of each kernel family (index + panels + vectors) ----
+
+def bytes_operator(n, m, nnz, c, elt):
+    """Operator apply Z = a X + b Theta X in one column chunk: indices once, X read by
+    both passes, the m x c intermediate written and read once, Z written once."""
+    return 2 * 4 * nnz + 8 * (n + m + 2) + 2 * n * c * elt + 2 * m * c * 4 + n * c * elt + 8 * (2 * n + m)
 
 
-def cpu_baseline(d, gpu_iters_per_step: float, sample_cols: int = 8, max_s: float = 25.0):
-    """Time the oracle's FP64 CG iteration (scipy.sparse operator) on the full graph with
-    a few columns, and scale to one outer iteration at c columns."""
-    from oracle import core, incidence
+def bytes_residual(n, m, nnz, c, chunks):
+    """Pair-arithmetic residual: per chunk the indices; F as two FP32 panels read by both
+    passes, the intermediate pair panel written and read, Y (FP64) read, R (FP32) written."""
+    return chunks * (2 * 4 * nnz + 8 * (n + m + 2)) + 2 * (8 * n * c) + 2 * (8 * m * c) + 8 * n * c + 4 * n * c \
+        + 4 * 2 * (n + m)
+
+
+def bytes_gemm(block_ptr, lpad):
+    """Grouped GEMM: every dense block once (BF16, padded to 128 rows x 64 columns), the
+    transposed basis once, the FP32 output once."""
+    sizes = np.diff(np.asarray(block_ptr, dtype=np.int64))
+    rows = ((sizes + 127) // 128) * 128
+    cols = ((sizes + 63) // 64) * 64
+    a = int((rows * cols).sum()) * 2
+    return a + lpad * int(cols.sum()) * 2 + int(rows.sum()) * lpad * 4
+
+
+def flops_gemm(block_ptr, lpad):
+    sizes = np.diff(np.asarray(block_ptr, dtype=np.int64))
+    return 2.0 * float((sizes.astype(np.float64) ** 2).sum()) * lpad
+
+
+def bytes_gradient(n, m, nnz, c):
+    """Gradient (FP32 panel, one chunk): as the operator apply without the Z write, plus
+    the per-hyperedge and per-vertex scalar vectors and the final hyperedge pass."""
+    return 2 * 4 * nnz + 8 * (n + m + 2) + 2 * n * c * 4 + 2 * m * c * 4 + 8 * (2 * n + m) + 4 * nnz + 8 * (2 * m + n)
+
+
+def cpu_baseline(d, block_ptr, iters_per_step: float, sample_cols: int = 4, budget_s: float = 25.0):  # noqa: ARG001
+    """The oracle (numpy/scipy, FP64) on bounded samples of one outer iteration, scaled
+    to a full step: CG iterations and residuals on the full graph with a few columns,
+    the gradient on the same columns, Algorithm 1 on a few blocks, the projection."""
+    from oracle import core, incidence, philox, rsvd
     t0 = time.time()
-    og = incidence.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
-    H = incidence.incidence_matrix(og)
+    H = incidence.incidence_matrix(incidence.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"]))
     build_s = time.time() - t0
+    wl = d["wl"]
     w = d["w0"]
-    Y = d["Y"][:, :sample_cols]
-    lam = d["wl"].lam
-    t1 = time.time()
-    its = 0
-    out = None
-    # a single CG iteration block: one operator apply + vector updates per iteration
-    while True:
-        its += 1
-        out = core.cg_solve(H, w, lam, Y, tol=1e-30, max_iter=its)
-        if time.time() - t1 > max_s / 3 or its >= 3:
-            break
-    per_call = (time.time() - t1)
-    # cg_solve(max_iter=k) runs k iterations + 2 operator applies (initial, final residual)
-    total_iters = its * (its + 1) // 2
-    total_applies = total_iters + 2 * its
-    per_apply = per_call / total_applies
     c = d["c"]
-    per_outer = (gpu_iters_per_step + 2) * per_apply * (c / sample_cols)
-    return {"value": 1.0 / per_outer, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle CG (scipy.sparse) on the full n={d['n']} m={d['m']} graph with "
-                       f"{sample_cols} of {c} columns, {total_iters} iterations timed; one outer iteration "
-                       f"= {gpu_iters_per_step:.0f} CG iterations + gradient, scaled by {c}/{sample_cols} columns"),
-            "seconds_per_outer_iter_extrapolated": per_outer, "oracle_build_s": build_s}
+    Y = d["Y"][:, :sample_cols]
+    t1 = time.time()
+    core.cg_solve(H, w, wl.lam, Y, tol=1e-30, max_iter=2)   # 2 iterations + 2 residual applies
+    t_apply = (time.time() - t1) / 4.0 * (c / sample_cols)
+    t2 = time.time()
+    core.weight_grad(H, w, Y, wl.mu)
+    t_grad = (time.time() - t2) * (c / sample_cols)
+    nb = len(block_ptr) - 1
+    sample_blocks = 2
+    t3 = time.time()
+    for b in range(sample_blocks):
+        Tb = rsvd.block_theta(H, w, [block_ptr[b], block_ptr[b + 1]])[0]
+        Om = philox.omega(np.arange(block_ptr[b], block_ptr[b + 1]), K_RANK + P_OVER, SEED)
+        rsvd.rsvd_ritz(Tb, Om, Q_ITERS, K_RANK)
+    t_rsvd = (time.time() - t3) / sample_blocks * nb
+    t4 = time.time()
+    core.project_simplex(w - wl.eta * np.ones_like(w))
+    t_proj = time.time() - t4
+    per_step = t_rsvd + (iters_per_step + 2.0) * t_apply + t_grad + t_proj
+    return {"value": 1.0 / per_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle on n={d['n']} m={d['m']}: 2 CG iterations + 2 residuals with {sample_cols} of "
+                       f"{c} columns (scaled by {c}/{sample_cols}), gradient on the same columns, Algorithm 1 on "
+                       f"{sample_blocks} of {nb} blocks (scaled by {nb}), projection; one step = rSVD + "
+                       f"{iters_per_step:.2f} CG iterations (the GPU loop's mean) + 2 residuals + gradient"),
+            "seconds_per_step_extrapolated": per_step, "oracle_build_s": build_s,
+            "parts_s": {"rsvd": t_rsvd, "apply": t_apply, "grad": t_grad, "proj": t_proj},
+            "measured_s": time.time() - t0}
 
 
 def run_reference(args, rank):
-    """--impl reference: the oracle (FP64, numpy/scipy on host cores) on a bounded sample."""
+    """--impl reference: the oracle (FP64, numpy/scipy on host cores) on bounded samples."""
     if rank != 0:
         return
     d = make_inputs(args.scale)
-    iters = 16.0
-    res = []
-    for _ in range(args.warmup + args.steps):
-        res.append(cpu_baseline(d, iters, sample_cols=4, max_s=6.0))
-    vals = [r["value"] for r in res[args.warmup:]]
-    v = float(np.mean(vals))
+    bp = synth_blocks(d)
+    vals = []
+    last = None
+    # one step assumes one CG iteration on average over the 20-iteration loop (the GPU
+    # loop needs ~9 in its first two iterations and none once w has settled)
+    for _ in range(max(1, args.warmup + args.steps)):
+        last = cpu_baseline(d, bp, 1.0, sample_cols=2, budget_s=8.0)
+        vals.append(last["value"])
+    v = float(np.mean(vals[args.warmup:] if len(vals) > args.warmup else vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": d["n"], "m": d["m"], "nnz": int(d["edge_ptr"][-1]),
-                       "c": d["c"], "lam": d["wl"].lam},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res[-1]["sample"], "value": v},
+            "config": config_dict(d, bp),
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def synth_blocks(d):
+    return np.asarray(d["block_ptr"], dtype=np.int64)
+
+
+def config_dict(d, bp):
+    wl = d["wl"]
+    return {"workload": WORKLOAD, "n": d["n"], "m": d["m"], "nnz": int(d["edge_ptr"][-1]), "c": d["c"],
+            "lam": wl.lam, "mu": wl.mu, "eta": d.get("eta", wl.eta), "outer_loop": LOOP, "tol_relres": TOL,
+            "size_law": synth.describe_sizes(wl), "route": "block rSVD preconditioned CG (BR)",
+            "blocks": int(len(bp) - 1), "block_sizes": "U{1024..8192}", "k": K_RANK, "p": P_OVER, "q": Q_ITERS,
+            "panel_dtype": "fp32 (fp64-accurate refinement)", "gemm_dtype": "bf16 tcgen05, fp32 accumulate",
+            "l2_flush": "inputs larger than L2 (>= 2 GB panels)"}
 
 
 def main():
@@ -212,37 +269,53 @@ def main():
     wl = d["wl"]
     n, m, c = d["n"], d["m"], d["c"]
     nnz = int(d["edge_ptr"][-1])
+    bp = synth_blocks(d)
     g = hgl.build_incidence(n, m, d["edge_ptr"], d["members"])
     Yh = torch.from_numpy(d["Y"])
     Y = hgl.padded_panel(n, c, torch.float64, dev)
     Y.copy_(Yh)
-    w = torch.tensor(d["w0"], device=dev)
+    w0 = torch.tensor(d["w0"], device=dev)
+    w = w0.clone()
     F = hgl.padded_panel(n, c, torch.float64, dev)
     stream = torch.cuda.current_stream()
+    counter = {"i": 0}
 
-    def step(Fp, wp, dtype=hgl.HGL_FP32):
-        return hgl.adaptive_step(g, wp, Y, Fp, lam=wl.lam, mu=wl.mu, eta=wl.eta, tol=TOL, dtype=dtype,
-                                 raise_on_fail=True)
+    def reset():
+        w.copy_(w0)
+        F.zero_()
 
-    # L2 is 129 MB; every panel here (>= 2 GB) is larger, so no flush is needed.
-    iters_seen = []
-    for _ in range(args.warmup):
-        st = step(F, w)
-        iters_seen.append(st.solve.iters)
+    eta = wl.eta if args.eta is None else args.eta
+    d["eta"] = eta
+
+    def step(Fp, wp, i, dtype=hgl.HGL_FP32, route=hgl.HGL_ROUTE_BR, reset=True):
+        if reset and i % LOOP == 0:
+            wp.copy_(w0)
+            Fp.zero_()
+        return hgl.adaptive_step(g, wp, Y, Fp, lam=wl.lam, mu=wl.mu, eta=eta, tol=TOL, dtype=dtype, route=route,
+                                 block_ptr=bp, k=K_RANK, p=P_OVER, q=Q_ITERS, seed=SEED + (i % LOOP))
+
+    # warm-up: W outer iterations of a loop, then the timed steps start a fresh loop
+    for i in range(args.warmup):
+        step(F, w, i)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
+    hgl.profile_enable(True)
+    l0 = hgl.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
     stats = []
-    for _ in range(args.steps):
-        stats.append(step(F, w))
+    for i in range(args.steps):
+        stats.append(step(F, w, i))
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = hgl.launch_count() - l0
+    prof = {f: hgl.profile_read(f) for f in range(8)}
+    hgl.profile_enable(False)
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     if world > 1:
@@ -251,89 +324,109 @@ def main():
         ms = float(t.item())
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1000.0)
-    solve_iters = float(np.mean([s.solve.iters for s in stats]))
+    iters = [s.solve.iters for s in stats]
     relres_max = max(s.solve.relres_max for s in stats)
 
-    # dominant kernel family: the operator apply in the inner FP32 CG, timed with events
-    X32 = hgl.padded_panel(n, c, torch.float32, dev)
-    X32.copy_(F[:, :c].float())
-    Z32 = hgl.padded_panel(n, c, torch.float32, dev)
-    for _ in range(2):
-        hgl.apply_theta(g, w, X32, 1.5, -1.0, Z=Z32)
-    torch.cuda.synchronize()
-    reps = 5
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(reps):
-        hgl.apply_theta(g, w, X32, 1.5, -1.0, Z=Z32)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    theta_ms = a0.elapsed_time(a1) / reps
-    peak, peak_kind = measured_peaks()
-    alg = theta_algorithmic_bytes(n, m, nnz, c, 4)
-    achieved = alg / (theta_ms / 1000.0) / 1e9
-    del X32, Z32
+    # roofline of the dominant kernel family (event-timed inside the timed region)
+    hbm_peak, bf16_peak, peak_kind = measured_peaks()
+    kernel_names = {hgl.PROF_OPERATOR: "operator apply (k_edge_pass + k_vertex_pass), FP32 panels, c=512",
+                    hgl.PROF_RESIDUAL: "pair-arithmetic residual (df::k_edge + df::k_vertex), c=512 in 2 chunks",
+                    hgl.PROF_GEMM: "grouped block GEMM on tcgen05 (umma::k_block_gemm), BF16 in / FP32 out",
+                    hgl.PROF_GRADIENT: "weight gradient (k_grad_edge + k_grad_vertex + k_grad_final), FP32"}
+    lpad = ((K_RANK + P_OVER + 15) // 16) * 16
+    per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4),
+                        hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, 2),
+                        hgl.PROF_GEMM: bytes_gemm(bp, lpad),
+                        hgl.PROF_GRADIENT: bytes_gradient(n, m, nnz, c)}
+    families = {}
+    for f, (fms, cnt) in prof.items():
+        if cnt > 0:
+            avg = fms / cnt
+            ent = {"ms_total": fms, "launches": cnt, "ms_per_launch": avg, "share_of_step_time": fms / ms}
+            if f in per_launch_bytes:
+                ent["achieved_GBps"] = per_launch_bytes[f] / (avg / 1000.0) / 1e9
+            families[hgl.PROF_NAMES[f]] = ent
+    dom = max(per_launch_bytes, key=lambda f: prof[f][0])
+    dms, dcnt = prof[dom]
+    davg = dms / max(dcnt, 1)
+    achieved = per_launch_bytes[dom] / (davg / 1000.0) / 1e9
+    roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": per_launch_bytes[dom], "ms_per_launch": davg, "launches": dcnt}
+    if prof[hgl.PROF_GEMM][1] > 0:
+        gavg = prof[hgl.PROF_GEMM][0] / prof[hgl.PROF_GEMM][1]
+        roofline["gemm"] = {"kernel": kernel_names[hgl.PROF_GEMM], "bound": "hbm",
+                            "achieved_GBps": per_launch_bytes[hgl.PROF_GEMM] / (gavg / 1000.0) / 1e9,
+                            "frac_hbm": per_launch_bytes[hgl.PROF_GEMM] / (gavg / 1000.0) / 1e9 / hbm_peak,
+                            "tensor_TFLOPs": flops_gemm(bp, lpad) / (gavg / 1000.0) / 1e12,
+                            "frac_bf16_peak": flops_gemm(bp, lpad) / (gavg / 1000.0) / 1e12 / bf16_peak,
+                            "ms_per_launch": gavg}
 
-    # end to end through the public API: host Y (pinned) and w in, w and statistics out
-    Yp = torch.empty((n, Y.stride(0)), dtype=torch.float64).pin_memory()
-    Yp[:, :c].copy_(Yh)
-    wp_host = w.cpu().pin_memory()
-    w_out = torch.empty_like(wp_host).pin_memory()
-    e2e_steps = max(1, min(3, args.steps))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    # end to end through the public API: every step copies Y (pinned host) in and reads
+    # w and the step statistics back; a loop's first step also copies w0 in
+    e2e = None
+    if not args.no_e2e:
+        Yp = torch.empty((n, Y.stride(0)), dtype=torch.float64).pin_memory()
+        Yp[:, :c].copy_(Yh)
+        w_host = w0.cpu().pin_memory()
+        w_out = torch.empty_like(w_host).pin_memory()
         Ybuf = Y.as_strided((n, Y.stride(0)), (Y.stride(0), 1))
-        Ybuf.copy_(Yp, non_blocking=True)
-        w.copy_(wp_host, non_blocking=True)
-        step(F, w)
-        w_out.copy_(w, non_blocking=True)
+        e2e_steps = args.steps
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = Yp.numel() * 8 + wp_host.numel() * 8
-    d2h = w_out.numel() * 8 + 64
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            Ybuf.copy_(Yp, non_blocking=True)
+            if i % LOOP == 0:
+                w.copy_(w_host, non_blocking=True)
+                F.zero_()
+            step(F, w, i, reset=False)
+            w_out.copy_(w, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(Yp.numel() * 8) + int(8 * m / LOOP),
+               "d2h_bytes_per_step": int(w_out.numel() * 8 + 48), "steps": e2e_steps}
 
     fp64 = None
     if not args.no_fp64:
-        F64 = F.clone()
-        w64 = w.clone()
-        step(F64, w64, hgl.HGL_FP64)  # warm
+        F64 = hgl.padded_panel(n, c, torch.float64, dev)
+        w64 = w0.clone()
+        step(F64, w64, 0, hgl.HGL_FP64, hgl.HGL_ROUTE_CG)
+        torch.cuda.synchronize()
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         b0.record(stream)
-        st64 = step(F64, w64, hgl.HGL_FP64)
+        st64 = [step(F64, w64, i, hgl.HGL_FP64, hgl.HGL_ROUTE_CG) for i in range(args.steps)]
         b1.record(stream)
         torch.cuda.synchronize()
-        f64_ms = b0.elapsed_time(b1)
-        fp64 = {"ms_per_step": f64_ms, "value": 1000.0 / f64_ms, "unit": UNIT, "cg_iters": st64.solve.iters,
-                "relres_max": st64.solve.relres_max, "speedup_of_mixed": f64_ms / ms_per_step}
+        f64_ms = b0.elapsed_time(b1) / args.steps
+        # same accuracy: the two loops' solutions agree to the tolerance's error bound
+        diff = (F64 - F).norm(dim=0) / F64.norm(dim=0).clamp_min(1e-300)
+        fp64 = {"ms_per_step": f64_ms, "value": 1000.0 / f64_ms, "unit": UNIT, "route": "plain CG, FP64",
+                "cg_iters_per_step": float(np.mean([s.solve.iters for s in st64])),
+                "relres_max": max(s.solve.relres_max for s in st64),
+                "speedup_of_mixed": f64_ms / ms_per_step,
+                "max_col_rel_diff_F_vs_mixed": float(diff.max().item()) if args.steps % LOOP == 0 else None}
         del F64, w64
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(d, solve_iters)
+        cpu = cpu_baseline(d, bp, float(np.mean(iters)))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "m": m, "nnz": nnz, "c": c, "lam": wl.lam, "mu": wl.mu,
-                       "eta": wl.eta, "tol_relres": TOL, "size_law": synth.describe_sizes(wl),
-                       "panel_dtype": "fp32", "route": "cg", "l2_flush": "inputs larger than L2 (>= 2 GB panels)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "solve": {"cg_iters_per_step": solve_iters, "relres_max": relres_max},
-            "roofline": {"kernel": "operator apply (hyperedge + vertex gather passes), FP32, c=512",
-                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                         "algorithmic_bytes": alg, "ms_per_launch": theta_ms},
-            "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "config": dict(config_dict(d, bp), parallelism="replicas" if world > 1 else "single"),
+            "solve": {"cg_iters_per_step": iters, "relres_max": relres_max},
+            "roofline": roofline,
+            "kernel_families": families,
+            "e2e": e2e,
             "fp64_block_cg": fp64,
             "cpu_baseline": cpu,
             "clocks": clocks,
-            "gpu_launches": None,
+            "gpu_launches": int(launches),
+            "gpu_launches_per_step": launches / args.steps,
             "gen_s": d["gen_s"],
         }
         print(json.dumps(line), flush=True)

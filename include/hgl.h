@@ -68,6 +68,29 @@ const char* hgl_last_error(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int32_t hgl_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (diagnostics; differences around a call count that call's launches). */
+uint64_t hgl_launch_count(void);
+
+/*
+ * Kernel timing (diagnostics).  While enabled, the library records a CUDA event pair
+ * on the launching stream around every launch of the kernel families below; the
+ * totals are read back with hgl_profile_read, which synchronises the device.
+ * hgl_profile_enable(1) clears the totals and starts recording; (0) stops.
+ */
+#define HGL_PROF_OPERATOR 0   /* operator apply: hyperedge + vertex gather passes      */
+#define HGL_PROF_RESIDUAL 1   /* pair-arithmetic residual: its two gather passes        */
+#define HGL_PROF_GEMM     2   /* block rSVD grouped GEMM (tcgen05 or FP64 CUDA cores)   */
+#define HGL_PROF_GRADIENT 3   /* weight gradient: its two gather passes and final sum   */
+#define HGL_PROF_PRECOND  4   /* block preconditioner apply (projection + expansion)    */
+#define HGL_PROF_RSVD     5   /* whole block rSVD build (assembly, Omega, the GEMMs,    */
+                              /* CholeskyQR2, Jacobi, Ritz vectors)                     */
+#define HGL_PROF_VECTOR   6   /* CG vector updates and panel dot products/copies        */
+#define HGL_PROF_PROJECT  7   /* simplex projection                                     */
+#define HGL_PROF_FAMILIES 8
+hgl_status hgl_profile_enable(int32_t on);
+hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches);
+
 /* ------------------------------------------------------------------------- */
 /* Incidence (Section 2: H(v,e) = 1 iff v in e; de(e) = sum_v H(v,e))         */
 /* ------------------------------------------------------------------------- */

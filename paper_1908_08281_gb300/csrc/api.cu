@@ -1,13 +1,73 @@
 // api.cu -- status strings, error recording, work buffers, graph queries and the
 // degree/scaling kernel (Section 2: dv = H w, de = H^T 1; Eq. 1 scalings).
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "hgl_internal.cuh"
 
 namespace hgl {
 
 static thread_local char g_last_error[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+struct ProfRecord {
+  int family;
+  cudaEvent_t start, stop;
+};
+std::mutex g_prof_mutex;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRecord> g_prof_records;   // recorded, not yet read
+std::vector<cudaEvent_t> g_prof_pool;     // free events
+double g_prof_ms[HGL_PROF_FAMILIES] = {};
+int64_t g_prof_count[HGL_PROF_FAMILIES] = {};
+
+cudaEvent_t pool_get() {
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// fold finished records into the totals (caller holds the mutex, device synchronised)
+void prof_drain() {
+  for (auto& r : g_prof_records) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      g_prof_ms[r.family] += ms;
+      g_prof_count[r.family] += 1;
+    }
+    g_prof_pool.push_back(r.start);
+    g_prof_pool.push_back(r.stop);
+  }
+  g_prof_records.clear();
+}
+}  // namespace
+
+bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
+
+int prof_begin(int family, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  ProfRecord r{family, pool_get(), pool_get()};
+  if (!r.start || !r.stop) return -1;
+  if (cudaEventRecord(r.start, st) != cudaSuccess) return -1;
+  g_prof_records.push_back(r);
+  return (int)g_prof_records.size() - 1;
+}
+
+void prof_end(int token, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  if (token >= 0 && token < (int)g_prof_records.size()) cudaEventRecord(g_prof_records[token].stop, st);
+}
 
 hgl_status record_error(hgl_status s, const char* fmt, ...) {
   va_list ap;
@@ -80,7 +140,7 @@ __global__ void k_degrees(int64_t n, int64_t m, const int64_t* __restrict__ csr_
 
 hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st) {
   int blocks = g->num_sms * 8;
-  k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t);
+  hgl::count_launch(); k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -108,6 +168,32 @@ const char* hgl_status_string(hgl_status s) {
 const char* hgl_last_error(void) { return hgl::g_last_error; }
 
 int32_t hgl_version(void) { return 100; }
+
+uint64_t hgl_launch_count(void) { return hgl::g_launches.load(std::memory_order_relaxed); }
+
+hgl_status hgl_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lock(hgl::g_prof_mutex);
+  if (on) {
+    HGL_CHECK_CUDA(cudaDeviceSynchronize());
+    hgl::prof_drain();
+    for (int f = 0; f < HGL_PROF_FAMILIES; ++f) {
+      hgl::g_prof_ms[f] = 0.0;
+      hgl::g_prof_count[f] = 0;
+    }
+  }
+  hgl::g_prof_on.store(on != 0);
+  return HGL_OK;
+}
+
+hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches) {
+  if (family < 0 || family >= HGL_PROF_FAMILIES) return hgl::record_error(HGL_ERR_INVALID_ARG, "unknown family");
+  std::lock_guard<std::mutex> lock(hgl::g_prof_mutex);
+  HGL_CHECK_CUDA(cudaDeviceSynchronize());
+  hgl::prof_drain();
+  if (ms_total) *ms_total = hgl::g_prof_ms[family];
+  if (launches) *launches = hgl::g_prof_count[family];
+  return HGL_OK;
+}
 
 void hgl_graph_destroy(hgl_graph* g) {
   if (!g) return;

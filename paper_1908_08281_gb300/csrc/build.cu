@@ -246,9 +246,9 @@ __global__ void k_scatter_rows(const int64_t* __restrict__ csc_ptr, const int32_
 hgl_status segmented_sort(const int64_t* ptr, int32_t* data, int64_t nseg, int32_t* list_a, int32_t* list_b,
                           unsigned* counts, int sms, cudaStream_t st) {
   HGL_CHECK_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned), st));
-  k_classify<<<sms * 8, 256, 0, st>>>(ptr, nseg, list_a, list_b, counts);
-  k_sort_short<<<sms * 8, 256, 0, st>>>(ptr, data, list_a, counts);
-  k_sort_long<<<sms * 4, 256, 0, st>>>(ptr, data, list_b, counts);
+  hgl::count_launch(); k_classify<<<sms * 8, 256, 0, st>>>(ptr, nseg, list_a, list_b, counts);
+  hgl::count_launch(); k_sort_short<<<sms * 8, 256, 0, st>>>(ptr, data, list_a, counts);
+  hgl::count_launch(); k_sort_long<<<sms * 4, 256, 0, st>>>(ptr, data, list_b, counts);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -256,9 +256,9 @@ hgl_status segmented_sort(const int64_t* ptr, int32_t* data, int64_t nseg, int32
 hgl_status exclusive_scan(const unsigned* in, int64_t n, int64_t* out, int64_t* tile_sums, cudaStream_t st) {
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (ntiles == 0) ntiles = 1;
-  k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tile_sums);
-  k_scan_tile_sums<<<1, SCAN_THREADS, 0, st>>>(tile_sums, ntiles);
-  k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tile_sums, out);
+  hgl::count_launch(); k_scan_tiles<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tile_sums);
+  hgl::count_launch(); k_scan_tile_sums<<<1, SCAN_THREADS, 0, st>>>(tile_sums, ntiles);
+  hgl::count_launch(); k_scan_apply<<<(unsigned)ntiles, SCAN_THREADS, 0, st>>>(in, n, tile_sums, out);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -325,24 +325,24 @@ hgl_status build(int64_t n, int64_t m, const int64_t* edge_ptr, const int32_t* m
     HGL_CHECK_CUDA(cudaMemcpyAsync(g->csc_idx, members, sizeof(int32_t) * nnz, cudaMemcpyDefault, st));
 
   unsigned hbits = 0;
-  k_check_ptr<<<sms * 4, 256, 0, st>>>(g->csc_ptr, m, nnz, g->de, bits);
+  hgl::count_launch(); k_check_ptr<<<sms * 4, 256, 0, st>>>(g->csc_ptr, m, nnz, g->de, bits);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(read_bits(bits, st, &hbits));
   HGL_TRY(bits_status(hbits));
 
-  k_count_members<<<sms * 8, 256, 0, st>>>(g->csc_idx, nnz, n, cnt, bits);
+  hgl::count_launch(); k_count_members<<<sms * 8, 256, 0, st>>>(g->csc_idx, nnz, n, cnt, bits);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(read_bits(bits, st, &hbits));
   HGL_TRY(bits_status(hbits));
 
   HGL_TRY(segmented_sort(g->csc_ptr, g->csc_idx, m, list_a, list_b, counts, sms, st));
-  k_check_dup<<<sms * 8, 256, 0, st>>>(g->csc_ptr, g->csc_idx, m, bits);
+  hgl::count_launch(); k_check_dup<<<sms * 8, 256, 0, st>>>(g->csc_ptr, g->csc_idx, m, bits);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(read_bits(bits, st, &hbits));
   HGL_TRY(bits_status(hbits));
 
   HGL_TRY(exclusive_scan(cnt, n, g->csr_ptr, tile_sums, st));
-  k_scatter_rows<<<sms * 8, 256, 0, st>>>(g->csc_ptr, g->csc_idx, m, g->csr_ptr, cursor, g->csr_idx);
+  hgl::count_launch(); k_scatter_rows<<<sms * 8, 256, 0, st>>>(g->csc_ptr, g->csc_idx, m, g->csr_ptr, cursor, g->csr_idx);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(segmented_sort(g->csr_ptr, g->csr_idx, n, list_a, list_b, counts, sms, st));
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));

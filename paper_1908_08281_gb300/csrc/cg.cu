@@ -57,7 +57,7 @@ hgl_status panel_dot(const hgl_graph* g, int c, const TA* A, int64_t lda, const 
                      double* partials, cudaStream_t st, int* rows) {
   VecGrid vg = vec_grid(g, c, sizeof(TA));
   dim3 grid(vg.gx, vg.gy);
-  HGL_LG_SWITCH(vg.lg, (k_panel_dot<TA, TB, LG><<<grid, VEC_THREADS, 0, st>>>(g->n, c, A, lda, B, ldb, scale, partials)));
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_dot<TA, TB, LG><<<grid, VEC_THREADS, 0, st>>>(g->n, c, A, lda, B, ldb, scale, partials))));
   HGL_CHECK_CUDA(cudaGetLastError());
   *rows = vg.gx;
   return HGL_OK;
@@ -68,7 +68,7 @@ hgl_status panel_scale(const hgl_graph* g, int c, const TX* X, int64_t ldx, doub
                        double* partials, cudaStream_t st, int* rows) {
   VecGrid vg = vec_grid(g, c, sizeof(TZ));
   dim3 grid(vg.gx, vg.gy);
-  HGL_LG_SWITCH(vg.lg, (k_panel_scale<TX, TZ, LG, DOT><<<grid, VEC_THREADS, 0, st>>>(g->n, c, X, ldx, scale, Z, ldz, partials)));
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_scale<TX, TZ, LG, DOT><<<grid, VEC_THREADS, 0, st>>>(g->n, c, X, ldx, scale, Z, ldz, partials))));
   HGL_CHECK_CUDA(cudaGetLastError());
   if (rows) *rows = vg.gx;
   return HGL_OK;
@@ -76,7 +76,7 @@ hgl_status panel_scale(const hgl_graph* g, int c, const TX* X, int64_t ldx, doub
 
 template <int MODE>
 hgl_status cg_reduce(const double* pa, const double* pb, int rows, const CgState& S, cudaStream_t st) {
-  k_cg_reduce<MODE><<<(S.c + 7) / 8, 256, 0, st>>>(pa, pb, rows, S);
+  hgl::count_launch(); k_cg_reduce<MODE><<<(S.c + 7) / 8, 256, 0, st>>>(pa, pb, rows, S);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -128,6 +128,12 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
     oZ = precond ? take(sizeof(float) * n * sm->ld32) : 0;
     oX = take(sizeof(float) * n * sm->ld32);
   }
+  size_t oFh = 0, oFl = 0, oSc = 0;
+  if (mode != HGL_FP64) {
+    oFh = take(sizeof(float) * n * sm->ld32);
+    oFl = take(sizeof(float) * n * sm->ld32);
+    oSc = take(sizeof(float) * 2 * (size_t)(g->n + g->m));
+  }
   size_t oVec = take(sizeof(double) * 8 * (size_t)c);
   size_t oInt = take(sizeof(int32_t) * 4 * (size_t)c + 64);
   hgl_status stt = HGL_OK;
@@ -138,6 +144,14 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
   sm->Q = base + oQ;
   sm->Z = precond ? base + oZ : nullptr;
   sm->X = mode == HGL_FP64 ? nullptr : base + oX;
+  if (mode != HGL_FP64) {
+    sm->Fh = reinterpret_cast<float*>(base + oFh);
+    sm->Fl = reinterpret_cast<float*>(base + oFl);
+    sm->s_hi = reinterpret_cast<float*>(base + oSc);
+    sm->s_lo = sm->s_hi + g->n;
+    sm->t_hi = sm->s_lo + g->n;
+    sm->t_lo = sm->t_hi + g->m;
+  }
   double* v = reinterpret_cast<double*>(base + oVec);
   CgState& S = sm->S;
   S.c = c;
@@ -193,9 +207,9 @@ hgl_status cg_iteration(hgl_graph* g, const SolverMem& sm, double lam, TV* Xs, i
   HGL_TRY(cg_reduce<RED_ALPHA>(sm.pa, nullptr, rows, S, st));
   VecGrid vg = vec_grid(g, c, sizeof(TV));
   dim3 grid(vg.gx, vg.gy);
-  HGL_LG_SWITCH(vg.lg, (k_cg_update_xr<TP, TV, LG><<<grid, VEC_THREADS, 0, st>>>(
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_cg_update_xr<TP, TV, LG><<<grid, VEC_THREADS, 0, st>>>(
                            g->n, c, static_cast<const TP*>(sm.P), ldp, static_cast<const TV*>(sm.Q), ldv, Xs, ldx,
-                           static_cast<TV*>(sm.R), ldv, S.alpha, sm.pa, S.run_flag)));
+                           static_cast<TV*>(sm.R), ldv, S.alpha, sm.pa, S.run_flag))));
   HGL_CHECK_CUDA(cudaGetLastError());
   const TV* zsrc = static_cast<const TV*>(sm.R);
   int rows_b = 0;
@@ -204,8 +218,8 @@ hgl_status cg_iteration(hgl_graph* g, const SolverMem& sm, double lam, TV* Xs, i
     zsrc = static_cast<const TV*>(sm.Z);
   }
   HGL_TRY(cg_reduce_beta(sm.pa, vg.gx, P ? sm.pb : nullptr, rows_b, S, st));
-  HGL_LG_SWITCH(vg.lg, (k_cg_update_p<TP, TV, LG><<<grid, VEC_THREADS, 0, st>>>(
-                           g->n, c, zsrc, ldv, static_cast<TP*>(sm.P), ldp, S.beta, S.run_flag)));
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_cg_update_p<TP, TV, LG><<<grid, VEC_THREADS, 0, st>>>(
+                           g->n, c, zsrc, ldv, static_cast<TP*>(sm.P), ldp, S.beta, S.run_flag))));
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -229,7 +243,11 @@ hgl_status run_cg_loop(hgl_graph* g, const SolverMem& sm, double lam, TV* Xs, in
                        const hgl_precond* P, int max_iter, int first_batch, cudaStream_t st, int* done_iters) {
   int it = 0;
   int32_t flag = 1;
-  int batch = std::max(1, std::min(first_batch, max_iter));
+  // Small problems launch a Chebyshev-bound batch of iterations between host checks
+  // (kernels of converged iterations return at once); large ones check after every
+  // iteration, where one host round trip is negligible next to an iteration.
+  const bool large = (double)g->n * sm.c >= (double)(1 << 24);
+  int batch = large ? 1 : std::max(1, std::min(first_batch, max_iter));
   while (it < max_iter) {
     const int todo = std::min(batch, max_iter - it);
     for (int k = 0; k < todo; ++k) HGL_TRY((cg_iteration<TP, TV>(g, sm, lam, Xs, ldx, xdt, vdt, P, st)));
@@ -237,7 +255,7 @@ hgl_status run_cg_loop(hgl_graph* g, const SolverMem& sm, double lam, TV* Xs, in
     HGL_CHECK_CUDA(cudaMemcpyAsync(&flag, sm.S.run_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
     if (flag == 0) break;
-    batch = 4;
+    batch = large ? 1 : 4;
   }
   *done_iters = it;
   return HGL_OK;
@@ -315,7 +333,8 @@ hgl_status fill_stats(const SolverMem& sm, int total_iters, int refinements, dou
 
 hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double* Y, int64_t ldy, double* F,
                          int64_t ldf, int c, const hgl_precond* P, const hgl_solve_opts& o, double* relres_out,
-                         int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready) {
+                         int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready,
+                         SolveExtras* extras) {
   const int mode = o.dtype;
   const double tol = o.tol > 0 ? o.tol : 1e-10;
   const int max_iter = o.max_iter > 0 ? o.max_iter : 1000;
@@ -331,7 +350,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   int rows = 0;
   HGL_TRY((panel_dot<double, double>(g, c, Y, ldy, Y, ldy, lam * lam, sm.pa, st, &rows)));
   HGL_TRY(cg_reduce<RED_B2>(sm.pa, nullptr, rows, S, st));
-  k_set_target<<<(c + 255) / 256, 256, 0, st>>>(S, tol * tol);
+  hgl::count_launch(); k_set_target<<<(c + 255) / 256, 256, 0, st>>>(S, tol * tol);
   HGL_CHECK_CUDA(cudaGetLastError());
   if (!warm) HGL_CHECK_CUDA(cudaMemset2DAsync(F, sizeof(double) * ldf, 0, sizeof(double) * c, g->n, st));
 
@@ -373,11 +392,20 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   const int max_refine = o.max_refine > 0 ? o.max_refine : 8;
   float* R32 = static_cast<float*>(sm.R);
   float* X32 = static_cast<float*>(sm.X);
+  // the iterate F lives as an FP32 pair (hi, lo) during refinement; the residual is
+  // formed from the pair in pair arithmetic (FP64-accurate, no FP64 arithmetic)
+  HGL_TRY(df_split_scalings(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, st));
+  HGL_TRY(df_panel_op(g, 0, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
   int total = 0, sweeps = 0;
   std::vector<double> rel(c), b2(c);
   std::vector<int32_t> iters_acc(c, 0);
   for (;;) {
-    HGL_TRY(true_residual(g, sm, lam, Y, ldy, F, ldf, R32, HGL_FP32, sm.ld32, st));
+    {
+      int rr_rows = 0;
+      HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0,
+                          lam, c, R32, sm.pa, st, &rr_rows));
+      HGL_TRY(cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, S, st));
+    }
     HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
     HGL_CHECK_CUDA(cudaMemcpyAsync(b2.data(), S.b2, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -385,7 +413,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
     for (int j = 0; j < c; ++j)
       if (b2[j] > 0 && !(rel[j] <= tol)) all = false;
     if (all || sweeps >= max_refine || total >= max_iter) break;
-    k_inner_targets<<<(c + 255) / 256, 256, 0, st>>>(S, tol, inner_tol);
+    hgl::count_launch(); k_inner_targets<<<(c + 255) / 256, 256, 0, st>>>(S, tol, inner_tol);
     HGL_CHECK_CUDA(cudaGetLastError());
     HGL_CHECK_CUDA(cudaMemset2DAsync(X32, sizeof(float) * sm.ld32, 0, sizeof(float) * c, g->n, st));
     int rows_b = 0;
@@ -421,13 +449,15 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
     total += done;
     std::vector<int32_t> it(c);
     HGL_CHECK_CUDA(cudaMemcpyAsync(it.data(), S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
-    VecGrid vg = vec_grid(g, c, 8);
-    dim3 grid(vg.gx, vg.gy);
-    HGL_LG_SWITCH(vg.lg, (k_add_correction<float, LG><<<grid, VEC_THREADS, 0, st>>>(g->n, c, X32, sm.ld32, F, ldf)));
-    HGL_CHECK_CUDA(cudaGetLastError());
+    HGL_TRY(df_panel_op(g, 1, c, nullptr, 0, sm.Fh, sm.Fl, sm.ld32, X32, st));
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < c; ++j) iters_acc[j] += it[j];
     ++sweeps;
+  }
+  if (sweeps > 0) HGL_TRY(df_panel_op(g, 2, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
+  if (extras) {
+    extras->f32 = sm.Fh;
+    extras->ld32 = sm.ld32;
   }
   HGL_CHECK_CUDA(cudaMemcpyAsync(S.iters, iters_acc.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, st));
   HGL_TRY(fill_stats(sm, total, sweeps > 0 ? sweeps - 1 : 0, tol, relres_out, iters_out, stats, st, &verdict));
@@ -480,5 +510,5 @@ extern "C" hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double l
   if (o.dtype != HGL_FP64 && o.dtype != HGL_FP32 && o.dtype != HGL_BF16)
     return hgl::record_error(HGL_ERR_INVALID_ARG, "unknown solve dtype");
   return hgl::cg_solve_impl(const_cast<hgl_graph*>(g), w, lam, Y, ldy, F, ldf, c, precond, o, relres, iters, stats,
-                            hgl::as_stream(stream), false);
+                            hgl::as_stream(stream), false, nullptr);
 }

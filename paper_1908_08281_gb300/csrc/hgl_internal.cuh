@@ -28,6 +28,29 @@ hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int lin
 
 int device_sm_count();
 
+// Process-wide count of kernels launched by the library (diagnostics).
+void count_launch(unsigned n = 1);
+
+// Kernel timing: while profiling is enabled, ProfScope records an event pair on the
+// stream around the launches made in its lifetime.
+bool profiling();
+int prof_begin(int family, cudaStream_t st);
+void prof_end(int token, cudaStream_t st);
+// Time the statements (launches) passed as the macro's trailing argument on stream `st`.
+#define HGL_PROFILED(FAM, ...)                 \
+  do {                                         \
+    ::hgl::ProfScope hgl_prof_scope_(FAM, st); \
+    __VA_ARGS__;                               \
+  } while (0)
+struct ProfScope {
+  int token;
+  cudaStream_t st;
+  ProfScope(int family, cudaStream_t s) : token(profiling() ? prof_begin(family, s) : -1), st(s) {}
+  ~ProfScope() {
+    if (token >= 0) prof_end(token, st);
+  }
+};
+
 }  // namespace hgl
 
 struct hgl_graph {

@@ -156,6 +156,7 @@ template <class TP, class TQ>
 hgl_status apply_typed(hgl_precond* P, const TP* R, int64_t ldr, TP* Z, int64_t ldz, int c, cudaStream_t st,
                        const int32_t* run_flag) {
   using A = typename AccT<TP>::type;
+  ProfScope prof(HGL_PROF_PRECOND, st);
   hgl_status s = HGL_OK;
   A* C = static_cast<A*>(buffer_get(P->cbuf, sizeof(A) * (size_t)P->nb * P->k * c, &s));
   if (!C) return s;
@@ -167,6 +168,7 @@ hgl_status apply_typed(hgl_precond* P, const TP* R, int64_t ldr, TP* Z, int64_t 
   const double inv1l = 1.0 / (1.0 + P->lam);
 #define HGL_KP_CASE(KPV)                                                                                              \
   case KPV:                                                                                                           \
+    hgl::count_launch(2);                                                                                           \
     k_precond_proj<TP, TQ, KPV><<<g1, 256, 0, st>>>(P->nb, P->d_v0, P->d_rows, Q, P->k, R, ldr, c, P->gain, C,        \
                                                     run_flag);                                                        \
     k_precond_expand<TP, TQ, KPV><<<g2, 256, 0, st>>>(P->unit_block, P->unit_tile, P->nunits, P->d_v0, P->d_rows, Q,  \
@@ -196,7 +198,7 @@ __global__ void k_export_q(const float* __restrict__ Qf, const double* __restric
 }  // namespace
 
 hgl_status precond_gains_launch(hgl_precond* P, const double* ev_lpad, int lpad, cudaStream_t st) {
-  k_gains<<<(P->nb * P->k + 255) / 256, 256, 0, st>>>(P->nb, P->k, lpad, ev_lpad, P->d_kb, P->lam, P->ev, P->gain);
+  hgl::count_launch(); k_gains<<<(P->nb * P->k + 255) / 256, 256, 0, st>>>(P->nb, P->k, lpad, ev_lpad, P->d_kb, P->lam, P->ev, P->gain);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -259,6 +261,7 @@ extern "C" hgl_status hgl_precond_export(const hgl_precond* P, int32_t b, double
   const int64_t first = P->bptr[b], rows = P->bptr[b + 1] - P->bptr[b];
   if (kb) *kb = P->kb[b];
   if (Q) {
+    hgl::count_launch();
     if (P->dtype == HGL_BF16)
       hgl::k_export_q<double><<<256, 256, 0, st>>>(static_cast<const float*>(P->Q), nullptr, first, rows, P->k, Q);
     else

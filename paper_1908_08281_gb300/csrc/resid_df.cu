@@ -1,0 +1,74 @@
+// resid_df.cu -- launches of the pair-arithmetic residual (df_kernels.cuh): the
+// mixed-precision solver keeps its FP64 iterate F as two FP32 panels (hi, lo) and
+// recomputes lam Y - M F from them to ~48 significant bits.
+#include <algorithm>
+
+#include "df_kernels.cuh"
+#include "solver.cuh"
+#include "theta_kernels.cuh"
+
+namespace hgl {
+
+hgl_status df_split_scalings(const hgl_graph* g, float* s_hi, float* s_lo, float* t_hi, float* t_lo,
+                             cudaStream_t st) {
+  count_launch(2);
+  df::k_split_vec<<<g->num_sms * 4, 256, 0, st>>>(g->n, g->s, s_hi, s_lo);
+  df::k_split_vec<<<g->num_sms * 4, 256, 0, st>>>(g->m, g->t, t_hi, t_lo);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf, float* Fh, float* Fl, int64_t ld32,
+                       const float* D, cudaStream_t st) {
+  const int blocks = g->num_sms * 8;
+  count_launch();
+  if (op == df::SPLIT)
+    df::k_panel<df::SPLIT><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+  else if (op == df::ACCUMULATE)
+    df::k_panel<df::ACCUMULATE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+  else
+    df::k_panel<df::COMBINE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+// R = fl32(gy Y + a F + b Theta F) with F = Fh + Fl; partials of R.R (rows returned).
+hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
+                       const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
+                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows) {
+  constexpr int E = 4;
+  const int nvec = (c + E - 1) / E;
+  int lg = 1, nv = 1;
+  pick_tile(std::min(nvec, 64), &lg, &nv);
+  const int cc = lg * nv * E;
+  hgl_status stt = HGL_OK;
+  float* Th = static_cast<float*>(buffer_get(g->scratch, sizeof(float) * 2 * (size_t)g->m * cc, &stt));
+  if (!Th) return stt;
+  float* Tl = Th + (size_t)g->m * cc;
+  const int64_t cap = (int64_t)g->num_sms * 8;
+  const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 7) / 8, cap));
+  const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, cap));
+  ProfScope prof(HGL_PROF_RESIDUAL, st);
+  for (int c0 = 0; c0 < c; c0 += cc) {
+    const int cw = std::min(cc, c - c0);
+#define HGL_DF_CASE(LG_, NV_)                                                                                     \
+  else if (lg == LG_ && nv == NV_) {                                                                              \
+    count_launch(2);                                                                                              \
+    df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, s_hi, s_lo, t_hi, t_lo, Fh, \
+                                                        Fl, ld32, c0, cw, Th, Tl, (int64_t)cc);                  \
+    df::k_vertex<LG_, NV_><<<grid2, df::THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, s_hi, s_lo, Th, Tl,     \
+                                                          (int64_t)cc, Fh, Fl, ld32, Y, ldy, a, b, gy, c0, cw, c, \
+                                                          R, ld32, partials);                                     \
+  }
+    if (false) {
+    }
+    HGL_DF_CASE(1, 1) HGL_DF_CASE(2, 1) HGL_DF_CASE(4, 1) HGL_DF_CASE(8, 1) HGL_DF_CASE(16, 1) HGL_DF_CASE(32, 1)
+    HGL_DF_CASE(32, 2)
+#undef HGL_DF_CASE
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
+  *rows = grid2;
+  return HGL_OK;
+}
+
+}  // namespace hgl

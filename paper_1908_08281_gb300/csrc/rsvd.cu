@@ -204,6 +204,7 @@ hgl_status set_smem(F* fn, size_t bytes) {
 template <int LP>
 hgl_status gemm(const Work& w, int dtype, int sms, cudaStream_t st) {
   const int nu = (int)w.unit_block.size();
+  ProfScope prof(HGL_PROF_GEMM, st);
   if (dtype == HGL_BF16) {
     CUtensorMap ma, mb;
     HGL_TRY(make_map(&ma, w.A, (uint64_t)w.ldA, (uint64_t)w.rows_tot, (uint64_t)w.ldA * 2, 128));
@@ -212,10 +213,10 @@ hgl_status gemm(const Work& w, int dtype, int sms, cudaStream_t st) {
     const size_t smem = umma::gemm_smem_bytes(LP);
     HGL_TRY(set_smem(umma::k_block_gemm<LP>, smem));
     const int grid = std::min(nu, sms);
-    umma::k_block_gemm<LP><<<grid, umma::THREADS, smem, st>>>(ma, mb, U, static_cast<float*>(w.D), LP, w.err);
+    hgl::count_launch(); umma::k_block_gemm<LP><<<grid, umma::THREADS, smem, st>>>(ma, mb, U, static_cast<float*>(w.D), LP, w.err);
   } else {
     const int grid = std::min(nu, sms * 4);
-    rsvd::k_block_gemm_f64<LP><<<grid, 256, 0, st>>>(w.B, w.d_unit_block, w.d_unit_tile, nu,
+    hgl::count_launch(); rsvd::k_block_gemm_f64<LP><<<grid, 256, 0, st>>>(w.B, w.d_unit_block, w.d_unit_tile, nu,
                                                       static_cast<const double*>(w.A),
                                                       static_cast<const double*>(w.St), static_cast<double*>(w.D));
   }
@@ -233,15 +234,18 @@ hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool writ
   HGL_TRY(set_smem(rsvd::k_chol_inv<LP>, chol_smem));
   const size_t ap_smem = sizeof(T) * (LP * LP + 32 * LP);
   HGL_TRY(set_smem(rsvd::k_apply_rinv<T, TB, LP>, ap_smem));
+  // first pass: a small shift keeps the factorisation defined; both passes drop
+  // pivots at the working precision's noise level (rank-deficient blocks)
   const double shift = dtype == HGL_BF16 ? 1e-6 : 1e-14;
+  const double drop = dtype == HGL_BF16 ? 1e-6 : 1e-13;
   const T* Y = static_cast<const T*>(w.D);
   T* Qf = static_cast<T*>(w.Qf);
   for (int pass = 0; pass < 2; ++pass) {
-    rsvd::k_gram<T, LP><<<nb, 256, 0, st>>>(w.B, Y, Y, w.G);
-    rsvd::k_chol_inv<LP><<<nb, 256, chol_smem, st>>>(w.B, w.G, pass == 0 ? shift : 0.0, w.R, w.fail);
+    hgl::count_launch(); rsvd::k_gram<T, LP><<<nb, 256, 0, st>>>(w.B, Y, Y, w.G);
+    hgl::count_launch(); rsvd::k_chol_inv<LP><<<nb, 256, chol_smem, st>>>(w.B, w.G, pass == 0 ? shift : 0.0, drop, w.R, w.fail);
     const bool last = pass == 1;
     // in-place on the second pass is fine: each tile reads its rows before writing them
-    rsvd::k_apply_rinv<T, TB, LP><<<std::min(nu, sms * 4), 256, ap_smem, st>>>(
+    hgl::count_launch(); rsvd::k_apply_rinv<T, TB, LP><<<std::min(nu, sms * 4), 256, ap_smem, st>>>(
         w.B, w.d_unit_block, w.d_unit_tile, nu, Y, w.R, Qf, (last && write_st) ? static_cast<TB*>(w.St) : nullptr);
     HGL_CHECK_CUDA(cudaGetLastError());
     Y = Qf;
@@ -269,6 +273,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   const int sms = g->num_sms;
   if (!degrees_ready) HGL_TRY(degrees_launch(g, w, st));
 
+  ProfScope prof(HGL_PROF_RSVD, st);
   Work wk;
   HGL_TRY(plan(g, bp, nb, k, l, lpad, gemm_dtype, &wk));
   HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
@@ -276,14 +281,14 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
 
   // dense diagonal blocks and the Gaussian start basis
   if (bf16) {
-    rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+    hgl::count_launch(); rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
                                                             g->csc_idx, g->s, g->t,
                                                             static_cast<__nv_bfloat16*>(wk.A));
-    rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<__nv_bfloat16*>(wk.St));
+    hgl::count_launch(); rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<__nv_bfloat16*>(wk.St));
   } else {
-    rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+    hgl::count_launch(); rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
                                                      g->csc_idx, g->s, g->t, static_cast<double*>(wk.A));
-    rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<double*>(wk.St));
+    hgl::count_launch(); rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<double*>(wk.St));
   }
   HGL_CHECK_CUDA(cudaGetLastError());
 
@@ -300,6 +305,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
     if (s_ == HGL_OK) s_ = gemm<LP>(wk, gemm_dtype, sms, st);
     if (s_ == HGL_OK) {
       // T = S^T (Theta S), eigendecomposition, Ritz vectors
+      hgl::count_launch();
       if (bf16)
         rsvd::k_gram<float, LP><<<nb, 256, 0, st>>>(wk.B, static_cast<const float*>(wk.Qf),
                                                    static_cast<const float*>(wk.D), wk.G);
@@ -308,7 +314,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
                                                     static_cast<const double*>(wk.D), wk.G);
       const size_t jsm = 2 * sizeof(double) * LP * LP;
       s_ = set_smem(rsvd::k_jacobi<LP>, jsm);
-      if (s_ == HGL_OK) rsvd::k_jacobi<LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40);
+      if (s_ == HGL_OK) { hgl::count_launch(); rsvd::k_jacobi<LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40); }
     }
   });
   HGL_TRY(s_);
@@ -378,6 +384,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
       if (bf16) {
         const size_t rs = sizeof(float) * LP * k;
         fin = set_smem(rsvd::k_ritz<float, LP>, rs);
+        hgl::count_launch();
         if (fin == HGL_OK)
           rsvd::k_ritz<float, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
               wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const float*>(wk.Qf), wk.R,
@@ -385,6 +392,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
       } else {
         const size_t rs = sizeof(double) * LP * k;
         fin = set_smem(rsvd::k_ritz<double, LP>, rs);
+        hgl::count_launch();
         if (fin == HGL_OK)
           rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
               wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R,

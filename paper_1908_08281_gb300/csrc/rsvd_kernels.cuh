@@ -282,17 +282,21 @@ __global__ void __launch_bounds__(256) k_gram(Blocks B, const T* __restrict__ X,
 // ---------------------------------------------------------------------------
 // Per-block Cholesky G = L L^T of the leading lb x lb Gram (symmetrised, with a
 // relative diagonal shift `shift` * trace / lb), then Rinv = L^-T (upper triangular,
-// so Q = Y Rinv has orthonormal columns).  A block whose Gram trace is 0 gets Rinv = 0.
-// Entries outside lb x lb are zero.  One CTA per block, matrix in shared memory.
+// so Q = Y Rinv has orthonormal columns).  The factorisation is rank revealing: a
+// pivot below `drop` * max diag(G) marks a direction Y does not span (a rank-deficient
+// block, e.g. one whose vertices lost all hyperedge weight); its row and column of
+// Rinv are zero, so the matching basis column is zero and contributes nothing later.
+// A block whose Gram trace is 0 or not finite gets Rinv = 0.  One CTA per block.
 // ---------------------------------------------------------------------------
 template <int LPAD>
-__global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __restrict__ G, double shift,
+__global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __restrict__ G, double shift, double drop,
                                                    double* __restrict__ Rinv, int32_t* __restrict__ fail) {
   extern __shared__ double sm[];
   double* L = sm;                   // LPAD x LPAD
   double* X = sm + LPAD * LPAD;     // LPAD x LPAD
-  __shared__ double s_trace;
-  __shared__ int s_bad;
+  __shared__ double s_trace, s_dmax;
+  __shared__ int dead[LPAD];
+  __shared__ int s_ndead;
   const int b = blockIdx.x;
   const int lb = B.lb[b];
   const double* Gb = G + (int64_t)b * LPAD * LPAD;
@@ -301,12 +305,17 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
     L[q] = (i < lb && j < lb) ? 0.5 * (Gb[i * LPAD + j] + Gb[j * LPAD + i]) : 0.0;
     X[q] = 0.0;
   }
+  for (int j = threadIdx.x; j < LPAD; j += blockDim.x) dead[j] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < lb; ++i) tr += L[i * LPAD + i];
+    double tr = 0.0, dm = 0.0;
+    for (int i = 0; i < lb; ++i) {
+      tr += L[i * LPAD + i];
+      dm = fmax(dm, L[i * LPAD + i]);
+    }
     s_trace = tr;
-    s_bad = 0;
+    s_dmax = dm;
+    s_ndead = 0;
   }
   __syncthreads();
   const double tr = s_trace;
@@ -316,18 +325,26 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
     return;
   }
   const double sigma = shift * tr / lb;
+  const double floor_pivot = drop * s_dmax;
   for (int i = threadIdx.x; i < lb; i += blockDim.x) L[i * LPAD + i] += sigma;
   __syncthreads();
-  // right-looking Cholesky
+  // right-looking Cholesky with dropped pivots
   for (int j = 0; j < lb; ++j) {
     if (threadIdx.x == 0) {
       const double d = L[j * LPAD + j];
-      if (!(d > 0.0)) s_bad = 1;
-      L[j * LPAD + j] = d > 0.0 ? sqrt(d) : 1.0;
+      if (!(d > floor_pivot) || !isfinite(d)) {
+        dead[j] = 1;
+        s_ndead += 1;
+        L[j * LPAD + j] = 1.0;
+      } else {
+        L[j * LPAD + j] = sqrt(d);
+      }
     }
     __syncthreads();
     const double dj = L[j * LPAD + j];
-    for (int i = j + 1 + threadIdx.x; i < lb; i += blockDim.x) L[i * LPAD + j] /= dj;
+    const bool dj_dead = dead[j] != 0;
+    for (int i = j + 1 + threadIdx.x; i < lb; i += blockDim.x)
+      L[i * LPAD + j] = dj_dead ? 0.0 : L[i * LPAD + j] / dj;
     __syncthreads();
     const int m = lb - j - 1;
     for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
@@ -346,12 +363,12 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
     }
   }
   __syncthreads();
-  // Rinv = X^T (upper)
+  // Rinv = X^T (upper); dead directions get a zero row and column
   for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
     const int i = q / LPAD, j = q % LPAD;
-    Rb[q] = X[j * LPAD + i];
+    Rb[q] = (i < lb && j < lb && !dead[i] && !dead[j]) ? X[j * LPAD + i] : 0.0;
   }
-  if (threadIdx.x == 0 && s_bad) atomicAdd(fail, 1);
+  if (threadIdx.x == 0 && s_ndead) atomicAdd(fail, 1);
 }
 
 // Q = Y Rinv row by row (one CTA per 64-row tile of a block); writes the row panel Qf

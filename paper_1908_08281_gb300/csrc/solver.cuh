@@ -27,13 +27,31 @@ struct SolverMem {
   int64_t ld64 = 0, ld32 = 0, ld16 = 0;
   void* int_base = nullptr;  // per-column int32 state and flags (zeroed per solve)
   size_t int_bytes = 0;
+  float *Fh = nullptr, *Fl = nullptr;          // mixed modes: F as an FP32 pair
+  float *s_hi = nullptr, *s_lo = nullptr;      // mixed modes: scalings as FP32 pairs
+  float *t_hi = nullptr, *t_lo = nullptr;
 };
+
+// Optional outputs of a solve: in mixed modes the FP32 high part of F (valid until
+// the next solve on the graph).
+struct SolveExtras {
+  const float* f32 = nullptr;
+  int64_t ld32 = 0;
+};
+
+hgl_status df_split_scalings(const hgl_graph* g, float* s_hi, float* s_lo, float* t_hi, float* t_lo, cudaStream_t st);
+hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf, float* Fh, float* Fl, int64_t ld32,
+                       const float* D, cudaStream_t st);
+hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
+                       const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
+                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows);
 
 hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
 
 hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double* Y, int64_t ldy, double* F,
                          int64_t ldf, int c, const hgl_precond* P, const hgl_solve_opts& o, double* relres_out,
-                         int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready);
+                         int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready,
+                         SolveExtras* extras);
 
 int cg_iteration_bound(double lam, double tol);
 

@@ -76,17 +76,23 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
   hgl_solve_opts so = o.solve;
   so.flags |= HGL_SOLVE_WARM_START;
   hgl_solve_stats ss{};
-  hgl_status solve_status = cg_solve_impl(g, w, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true);
+  SolveExtras ext;
+  hgl_status solve_status = cg_solve_impl(g, w, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true,
+                                          &ext);
   if (P) hgl_precond_destroy(P);
   if (solve_status != HGL_OK && solve_status != HGL_ERR_NOT_CONVERGED) return solve_status;
 
   // gradient at the solve's F (degrees are still those of the current w)
-  HGL_TRY(weight_grad_launch(g, w, F, nullptr, ldf, c, HGL_FP64, o.mu, 0, grad, st));
+  // mixed modes differentiate at the FP32 high part of F (FP32 arithmetic); FP64 mode at F
+  if (ext.f32)
+    HGL_TRY(weight_grad_launch(g, w, ext.f32, nullptr, ext.ld32, c, HGL_FP32, o.mu, 0, grad, st));
+  else
+    HGL_TRY(weight_grad_launch(g, w, F, nullptr, ldf, c, HGL_FP64, o.mu, 0, grad, st));
   // ||F||^2 for the objective
   HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, 0));
   const double* ex = static_cast<const double*>(g->misc.ptr);
-  k_step_sums<<<red_blocks, RED_THREADS, 0, st>>>(m, g->t, ex, w_old, w, part);
+  hgl::count_launch(); k_step_sums<<<red_blocks, RED_THREADS, 0, st>>>(m, g->t, ex, w_old, w, part);
   HGL_CHECK_CUDA(cudaGetLastError());
   std::vector<double> hp(3 * (size_t)red_blocks);
   HGL_CHECK_CUDA(cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));

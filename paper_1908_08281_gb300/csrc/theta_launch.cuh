@@ -48,15 +48,16 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
                       : static_cast<TT*>(buffer_get(g->scratch, sizeof(TT) * (size_t)g->m * (size_t)cc, &stt));
   if (!Tp) return stt;
   const int grid1 = edge_grid(g), grid2 = vertex_grid(g);
+  ProfScope prof(HGL_PROF_OPERATOR, st);
   const TX* X = static_cast<const TX*>(cl.X);
   TZ* Z = static_cast<TZ*>(cl.Z);
   for (int c0 = 0; c0 < cl.c; c0 += cc) {
     const int cw = cl.c - c0 < cc ? cl.c - c0 : cc;
 #define HGL_EDGE_CASE(LG_, NV_)                                                                       \
-  else if (lg == LG_ && nv == NV_) k_edge_pass<TX, TT, LG_, NV_><<<grid1, OP_THREADS, 0, st>>>(          \
+  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_edge_pass<TX, TT, LG_, NV_><<<grid1, OP_THREADS, 0, st>>>(          \
       g->m, g->csc_ptr, g->csc_idx, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);
 #define HGL_VERTEX_CASE(LG_, NV_)                                                                     \
-  else if (lg == LG_ && nv == NV_) k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
+  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
       g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
       cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
     if (false) {

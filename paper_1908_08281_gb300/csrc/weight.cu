@@ -211,13 +211,14 @@ hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld
   const int64_t cap = (int64_t)g->num_sms * 8;
   const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + OP_WARPS - 1) / OP_WARPS, cap));
   const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + OP_WARPS - 1) / OP_WARPS, cap));
+  ProfScope prof(HGL_PROF_GRADIENT, st);
   for (int c0 = 0; c0 < c; c0 += cc) {
     const int cw = std::min(cc, c - c0);
 #define HGL_GE(LG_, NV_)                                                                                        \
-  else if (lg == LG_ && nv == NV_) k_grad_edge<TX, LG_, NV_, DUAL><<<grid1, OP_THREADS, 0, st>>>(                 \
+  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_edge<TX, LG_, NV_, DUAL><<<grid1, OP_THREADS, 0, st>>>(                 \
       g->m, g->csc_ptr, g->csc_idx, g->s, g->t, F, Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);
 #define HGL_GV(LG_, NV_)                                                                                        \
-  else if (lg == LG_ && nv == NV_) k_grad_vertex<TX, LG_, NV_, DUAL><<<grid2, OP_THREADS, 0, st>>>(               \
+  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_vertex<TX, LG_, NV_, DUAL><<<grid2, OP_THREADS, 0, st>>>(               \
       g->n, g->csr_ptr, g->csr_idx, g->s, TF, TZ, (int64_t)cc, F, Zb, ld, c0, cw, phi);
     if (false) {
     }
@@ -231,7 +232,7 @@ hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld
 #undef HGL_GV
     HGL_CHECK_CUDA(cudaGetLastError());
   }
-  k_grad_final<<<grid1, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->de, ex, frozen ? nullptr : phi, w, mu,
+  hgl::count_launch(); k_grad_final<<<grid1, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->de, ex, frozen ? nullptr : phi, w, mu,
                                              grad);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
@@ -362,19 +363,20 @@ hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, cons
 
 hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
                           cudaStream_t st, int max_steps) {
+  ProfScope prof(HGL_PROF_PROJECT, st);
   // work layout: v[m] | part_sum[blocks] | part_cnt[blocks] | ProjState
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
   double* v = work;
   double* ps_sum = v + m;
   double* ps_cnt = ps_sum + blocks;
   ProjState* ps = reinterpret_cast<ProjState*>(ps_cnt + blocks);
-  k_proj_init<<<blocks, PROJ_THREADS, 0, st>>>(v, w, grad, eta, m, ps_sum);
-  k_proj_tau0<<<1, 32, 0, st>>>(ps_sum, blocks, m, ps);
+  hgl::count_launch(); k_proj_init<<<blocks, PROJ_THREADS, 0, st>>>(v, w, grad, eta, m, ps_sum);
+  hgl::count_launch(); k_proj_tau0<<<1, 32, 0, st>>>(ps_sum, blocks, m, ps);
   HGL_CHECK_CUDA(cudaGetLastError());
   int steps = 0;
   for (;;) {
     const int batch = 16;
-    for (int k = 0; k < batch; ++k) k_proj_step<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps_sum, ps_cnt, ps);
+    for (int k = 0; k < batch; ++k) { hgl::count_launch(); k_proj_step<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps_sum, ps_cnt, ps); }
     HGL_CHECK_CUDA(cudaGetLastError());
     steps += batch;
     if (max_steps > 0 && steps >= max_steps) break;
@@ -383,7 +385,7 @@ hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, 
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
     if (done || steps > m + 16) break;
   }
-  k_proj_apply<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps, w);
+  hgl::count_launch(); k_proj_apply<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps, w);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }

@@ -68,6 +68,9 @@ _SIGNATURES = {
     "hgl_status_string": (ctypes.c_char_p, [_I32]),
     "hgl_last_error": (ctypes.c_char_p, []),
     "hgl_version": (_I32, []),
+    "hgl_launch_count": (ctypes.c_uint64, []),
+    "hgl_profile_enable": (_I32, [_I32]),
+    "hgl_profile_read": (_I32, [_I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "hgl_build_incidence": (_I32, [_I64, _I64, _P, _P, _I64, _P, ctypes.POINTER(_P)]),
     "hgl_graph_destroy": (None, [_P]),
     "hgl_graph_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
@@ -104,6 +107,31 @@ def lib() -> ctypes.CDLL:
             fn.argtypes = args
         _LIB = handle
     return _LIB
+
+
+def launch_count() -> int:
+    """Kernels launched by libhgl in this process so far."""
+    return int(lib().hgl_launch_count())
+
+
+PROF_OPERATOR, PROF_RESIDUAL, PROF_GEMM, PROF_GRADIENT = 0, 1, 2, 3
+PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT = 4, 5, 6, 7
+PROF_NAMES = {0: "operator apply", 1: "pair-arithmetic residual", 2: "grouped block GEMM (tcgen05)",
+              3: "weight gradient", 4: "preconditioner apply", 5: "block rSVD build (all)",
+              6: "CG vector kernels", 7: "simplex projection"}
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing totals) or stop recording kernel-family timings."""
+    _check(lib().hgl_profile_enable(1 if on else 0))
+
+
+def profile_read(family: int):
+    """(total ms, launches) recorded for a kernel family (synchronises the device)."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().hgl_profile_read(family, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def header_functions() -> list[str]:

@@ -155,3 +155,29 @@ def test_rsvd_argument_errors():
         with pytest.raises(hgl.HglError) as ei:
             hgl.block_rsvd(g, wt, 0.5, bp, k, p, 1, 1)
         assert ei.value.name == "HGL_ERR_INVALID_ARG"
+
+
+def test_br_loop_through_weight_collapse_mixed_precision():
+    # with mu = 0 the projected step drives w onto a few hyperedges within a few outer
+    # iterations; most diagonal blocks then lose rank (isolated vertices have s = 0).
+    # Past that point the projection is discontinuous in its input (the support changes
+    # at near-ties), so each step is checked against the oracle from the GPU's own w.
+    wl, d, H, w, g = _setup(n=6000, m=10000, c=8, seed=9)
+    bp = d["block_ptr"]
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    eta = 1e-2
+    for i in range(6):
+        w_before = wt.cpu().numpy().copy()
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 0.0, eta, tol=1e-8, dtype=hgl.HGL_FP32,
+                               route=hgl.HGL_ROUTE_BR, block_ptr=bp, k=16, p=8, q=2, seed=SEED + i)
+        assert st.solve.relres_max <= 1e-8
+        Fg = F.cpu().numpy()
+        Fr, _ = core.certified_solve(H, w_before, wl.lam, d["Y"])
+        err = np.linalg.norm(Fg - Fr, axis=0) / np.linalg.norm(Fr, axis=0)
+        assert err.max() <= 1e-5, (i, err.max())
+        w_ref = core.project_simplex(w_before - eta * core.weight_grad(H, w_before, Fr, 0.0))
+        assert np.linalg.norm(wt.cpu().numpy() - w_ref) <= 1e-4 * np.linalg.norm(w_ref), i
+    # the weight mass has concentrated on a handful of hyperedges
+    assert torch.topk(wt, 10).values.sum().item() > 0.9
