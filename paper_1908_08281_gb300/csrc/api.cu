@@ -205,6 +205,7 @@ void hgl_graph_destroy(hgl_graph* g) {
   cudaFree(g->dv);
   cudaFree(g->s);
   cudaFree(g->t);
+  cudaFree(g->edge_order);
   hgl::buffer_free(g->scratch);
   hgl::buffer_free(g->scratch2);
   hgl::buffer_free(g->partials);

@@ -7,8 +7,10 @@
 // pointers; scatter hyperedge ids into vertex rows; sort every vertex row.  Every
 // output is a pure function of the input, so the result is bit-exact and the same
 // from run to run.
+#include <algorithm>
 #include <climits>
 #include <new>
+#include <vector>
 
 #include "hgl_internal.cuh"
 
@@ -278,6 +280,37 @@ hgl_status bits_status(unsigned b) {
   return HGL_OK;
 }
 
+// Hyperedges in decreasing size order (stable counting sort on the host; one-time).
+// The gather passes give each hyperedge above HEAVY_ROW members a whole thread block
+// and schedule the rest longest first, so no long row finishes last.
+hgl_status order_edges(hgl_graph* g, cudaStream_t st) {
+  const int64_t m = g->m;
+  std::vector<int64_t> ptr(m + 1);
+  HGL_CHECK_CUDA(cudaMemcpyAsync(ptr.data(), g->csc_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  int64_t maxs = 0;
+  for (int64_t e = 0; e < m; ++e) maxs = std::max(maxs, ptr[e + 1] - ptr[e]);
+  std::vector<int64_t> count(maxs + 2, 0);
+  for (int64_t e = 0; e < m; ++e) count[maxs - (ptr[e + 1] - ptr[e])]++;
+  int64_t acc = 0;
+  for (auto& x : count) {
+    const int64_t c = x;
+    x = acc;
+    acc += c;
+  }
+  std::vector<int32_t> order(m);
+  g->nheavy = 0;
+  for (int64_t e = 0; e < m; ++e) {
+    const int64_t sz = ptr[e + 1] - ptr[e];
+    order[count[maxs - sz]++] = (int32_t)e;
+    if (sz > HEAVY_ROW) g->nheavy++;
+  }
+  HGL_CHECK_CUDA(cudaMalloc(&g->edge_order, sizeof(int32_t) * m));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(g->edge_order, order.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  return HGL_OK;
+}
+
 struct TempMem {
   void* p = nullptr;
   ~TempMem() {
@@ -345,6 +378,7 @@ hgl_status build(int64_t n, int64_t m, const int64_t* edge_ptr, const int32_t* m
   hgl::count_launch(); k_scatter_rows<<<sms * 8, 256, 0, st>>>(g->csc_ptr, g->csc_idx, m, g->csr_ptr, cursor, g->csr_idx);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(segmented_sort(g->csr_ptr, g->csr_idx, n, list_a, list_b, counts, sms, st));
+  HGL_TRY(order_edges(g, st));
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   return HGL_OK;
 }

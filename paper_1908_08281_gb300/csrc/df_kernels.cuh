@@ -66,24 +66,31 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
 constexpr int THREADS = 256;
 
 // hyperedge pass: T[e] = t_e sum_{v in e} s_v F[v]     (F, T as hi/lo FP32 panels)
+// Heavy hyperedges (the first nheavy of `order`) get one block each; light ones one
+// warp each, longest first (as in the operator's hyperedge pass).
 template <int LG, int NV>
 __global__ void __launch_bounds__(THREADS)
 k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-       const float* __restrict__ s_hi, const float* __restrict__ s_lo, const float* __restrict__ t_hi,
-       const float* __restrict__ t_lo, const float* __restrict__ Fh, const float* __restrict__ Fl, int64_t ldf,
-       int c0, int cw, float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt) {
-  constexpr int E = 4, G = 32 / LG;
-  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = warp; e < m; e += nwarps) {
+       const int32_t* __restrict__ order, int64_t nheavy, const float* __restrict__ s_hi,
+       const float* __restrict__ s_lo, const float* __restrict__ t_hi, const float* __restrict__ t_lo,
+       const float* __restrict__ Fh, const float* __restrict__ Fl, int64_t ldf, int c0, int cw,
+       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt) {
+  constexpr int E = 4, G = 32 / LG, WARPS = THREADS / 32, TILE = LG * NV * E;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
+  f2 acc[NV][E];
+  const bool heavy = blockIdx.x < nheavy;
+  const int64_t warp = heavy ? 0 : (((int64_t)blockIdx.x - nheavy) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = heavy ? 1 : (((int64_t)gridDim.x - nheavy) * blockDim.x) >> 5;
+  for (int64_t q = heavy ? blockIdx.x : nheavy + warp; q < (heavy ? (int64_t)blockIdx.x + 1 : m); q += nwarps) {
+    const int32_t e = order[q];
     const int64_t beg = __ldg(csc_ptr + e), end = __ldg(csc_ptr + e + 1);
-    f2 acc[NV][E];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
       for (int j = 0; j < E; ++j) acc[k][j] = f2{0.f, 0.f};
-    for (int64_t i = beg + grp; i < end; i += G) {
+    const int64_t first = heavy ? beg + wid * G + grp : beg + grp;
+    const int64_t step = heavy ? (int64_t)WARPS * G : G;
+    for (int64_t i = first; i < end; i += step) {
       const int32_t v = __ldg(csc_idx + i);
       const f2 sv{__ldg(s_hi + v), __ldg(s_lo + v)};
 #pragma unroll
@@ -107,6 +114,28 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
           f2 o{__shfl_xor_sync(0xffffffffu, acc[k][j].hi, off), __shfl_xor_sync(0xffffffffu, acc[k][j].lo, off)};
           add2(acc[k][j], o);
         }
+    if (heavy) {
+      __shared__ float red_hi[WARPS][TILE], red_lo[WARPS][TILE];
+      if (grp == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+          for (int j = 0; j < E; ++j) {
+            red_hi[wid][(k * LG + l) * E + j] = acc[k][j].hi;
+            red_lo[wid][(k * LG + l) * E + j] = acc[k][j].lo;
+          }
+      __syncthreads();
+      if (wid != 0) return;
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          f2 sum{0.f, 0.f};
+          for (int w = 0; w < WARPS; ++w)
+            add2(sum, f2{red_hi[w][(k * LG + l) * E + j], red_lo[w][(k * LG + l) * E + j]});
+          acc[k][j] = sum;
+        }
+    }
     if (grp == 0) {
       const f2 te{t_hi[e], t_lo[e]};
 #pragma unroll

@@ -28,6 +28,9 @@ hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int lin
 
 int device_sm_count();
 
+// Rows (hyperedges) longer than this go to a whole thread block in the gather passes.
+constexpr int64_t HEAVY_ROW = 128;
+
 // Process-wide count of kernels launched by the library (diagnostics).
 void count_launch(unsigned n = 1);
 
@@ -73,6 +76,10 @@ struct hgl_graph {
   hgl::Buffer step;            // adaptive-step vectors (grad, w_old, projection work)
   hgl::Buffer rsvd;            // block rSVD work space (dense blocks, bases, Grams)
   int chunk_cols = 0;          // operator column chunk (0 = library default)
+  // hyperedges in decreasing size order; the first nheavy (size > HEAVY_ROW) are
+  // processed by a whole thread block each, the rest by one warp each in this order
+  int32_t* edge_order = nullptr;  // m
+  int64_t nheavy = 0;
 };
 
 #define HGL_CHECK_CUDA(call)                                                   \

@@ -46,7 +46,7 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
   if (!Th) return stt;
   float* Tl = Th + (size_t)g->m * cc;
   const int64_t cap = (int64_t)g->num_sms * 8;
-  const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 7) / 8, cap));
+  const int grid1 = (int)(g->nheavy + std::max<int64_t>(1, std::min<int64_t>((g->m - g->nheavy + 7) / 8, cap)));
   const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, cap));
   ProfScope prof(HGL_PROF_RESIDUAL, st);
   for (int c0 = 0; c0 < c; c0 += cc) {
@@ -54,8 +54,9 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
 #define HGL_DF_CASE(LG_, NV_)                                                                                     \
   else if (lg == LG_ && nv == NV_) {                                                                              \
     count_launch(2);                                                                                              \
-    df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, s_hi, s_lo, t_hi, t_lo, Fh, \
-                                                        Fl, ld32, c0, cw, Th, Tl, (int64_t)cc);                  \
+    df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy,   \
+                                                        s_hi, s_lo, t_hi, t_lo, Fh, Fl, ld32, c0, cw, Th, Tl,    \
+                                                        (int64_t)cc);                                            \
     df::k_vertex<LG_, NV_><<<grid2, df::THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, s_hi, s_lo, Th, Tl,     \
                                                           (int64_t)cc, Fh, Fl, ld32, Y, ldy, a, b, gy, c0, cw, c, \
                                                           R, ld32, partials);                                     \

@@ -89,6 +89,8 @@ struct Work {
   void* D = nullptr;      // rows_tot x lpad (FP32 or FP64)
   void* Qf = nullptr;     // rows_tot x lpad (FP32 or FP64)
   double* G = nullptr;    // nb x lpad x lpad
+  double* Gpart = nullptr;  // nb x max_splits x lpad x lpad partial Grams
+  int max_splits = 1;
   double* R = nullptr;    // nb x lpad x lpad
   double* ev = nullptr;   // nb x lpad
   int32_t* fail = nullptr;
@@ -140,7 +142,9 @@ hgl_status plan(hgl_graph* g, const int64_t* bp, int nb, int k, int l, int lpad,
   const size_t oSt = take(ea * (size_t)lpad * (size_t)w->Ktot);
   const size_t oD = take(ed * (size_t)w->rows_tot * lpad);
   const size_t oQf = take(ed * (size_t)w->rows_tot * lpad);
+  w->max_splits = (int)((maxb + rsvd::GRAM_SPLIT - 1) / rsvd::GRAM_SPLIT);
   const size_t oG = take(8 * (size_t)nb * lpad * lpad);
+  const size_t oGp = take(8 * (size_t)nb * w->max_splits * lpad * lpad);
   const size_t oR = take(8 * (size_t)nb * lpad * lpad);
   const size_t oEv = take(8 * (size_t)nb * lpad);
   const size_t oMeta = take(8 * 3 * (size_t)nb + 4 * 3 * (size_t)nb + 4 * 2 * nu + 64);
@@ -152,6 +156,7 @@ hgl_status plan(hgl_graph* g, const int64_t* bp, int nb, int k, int l, int lpad,
   w->D = base + oD;
   w->Qf = base + oQf;
   w->G = reinterpret_cast<double*>(base + oG);
+  w->Gpart = reinterpret_cast<double*>(base + oGp);
   w->R = reinterpret_cast<double*>(base + oR);
   w->ev = reinterpret_cast<double*>(base + oEv);
   char* meta = base + oMeta;
@@ -224,6 +229,17 @@ hgl_status gemm(const Work& w, int dtype, int sms, cudaStream_t st) {
   return HGL_OK;
 }
 
+// G = X^T Y per block (partials over row ranges, then a fixed-order sum)
+template <class T, int LP>
+hgl_status gram(const Work& w, const T* X, const T* Y, cudaStream_t st) {
+  const int nb = w.B.nb;
+  hgl::count_launch(2);
+  rsvd::k_gram_part<T, LP><<<nb * w.max_splits, 256, 0, st>>>(w.B, w.max_splits, X, Y, w.Gpart);
+  rsvd::k_gram_reduce<LP><<<nb, 256, 0, st>>>(w.B, w.max_splits, w.Gpart, w.G);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
 // Q = CholeskyQR2(D): G = D^T D, Rinv = chol^-T, Qf = D Rinv; again on Qf.  The final
 // pass also refreshes the transposed basis St (when write_st).
 template <class T, class TB, int LP>
@@ -241,7 +257,7 @@ hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool writ
   const T* Y = static_cast<const T*>(w.D);
   T* Qf = static_cast<T*>(w.Qf);
   for (int pass = 0; pass < 2; ++pass) {
-    hgl::count_launch(); rsvd::k_gram<T, LP><<<nb, 256, 0, st>>>(w.B, Y, Y, w.G);
+    HGL_TRY((gram<T, LP>(w, Y, Y, st)));
     hgl::count_launch(); rsvd::k_chol_inv<LP><<<nb, 256, chol_smem, st>>>(w.B, w.G, pass == 0 ? shift : 0.0, drop, w.R, w.fail);
     const bool last = pass == 1;
     // in-place on the second pass is fine: each tile reads its rows before writing them
@@ -306,14 +322,10 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
     if (s_ == HGL_OK) {
       // T = S^T (Theta S), eigendecomposition, Ritz vectors
       hgl::count_launch();
-      if (bf16)
-        rsvd::k_gram<float, LP><<<nb, 256, 0, st>>>(wk.B, static_cast<const float*>(wk.Qf),
-                                                   static_cast<const float*>(wk.D), wk.G);
-      else
-        rsvd::k_gram<double, LP><<<nb, 256, 0, st>>>(wk.B, static_cast<const double*>(wk.Qf),
-                                                    static_cast<const double*>(wk.D), wk.G);
+      s_ = bf16 ? gram<float, LP>(wk, static_cast<const float*>(wk.Qf), static_cast<const float*>(wk.D), st)
+                : gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
       const size_t jsm = 2 * sizeof(double) * LP * LP;
-      s_ = set_smem(rsvd::k_jacobi<LP>, jsm);
+      if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<LP>, jsm);
       if (s_ == HGL_OK) { hgl::count_launch(); rsvd::k_jacobi<LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40); }
     }
   });

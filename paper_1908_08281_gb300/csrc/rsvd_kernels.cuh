@@ -77,7 +77,13 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
     const int bs = B.rows[b];
     const int64_t width = ((int64_t)bs + 63) / 64 * 64;
     TA* row = A + r * B.ldA;
-    for (int64_t j = lane; j < width; j += 32) row[j] = from_double<TA>(0.0);
+    // zero the used width with 16-byte stores (rows start on 128-byte boundaries and
+    // the width is a multiple of 64 elements)
+    {
+      constexpr int PER = 16 / (int)sizeof(TA);
+      uint4* row4 = reinterpret_cast<uint4*>(row);
+      for (int64_t j = lane; j < width / PER; j += 32) row4[j] = make_uint4(0u, 0u, 0u, 0u);
+    }
     if (i >= bs) continue;
     __syncwarp();
     const int64_t v0 = B.v0[b];
@@ -150,31 +156,47 @@ __device__ __forceinline__ double unit53(uint32_t a, uint32_t b) {
   return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6) + 0.5) * 0x1p-53;
 }
 
-// Omega[g, j] for global row g and column j (Box-Muller on one Philox draw per pair).
-__device__ __forceinline__ double omega_entry(int64_t g, int j, uint64_t seed) {
-  uint32_t c[4] = {(uint32_t)g, (uint32_t)(j >> 1), OMEGA_STREAM, 0u};
+// Omega[g, 2p] and Omega[g, 2p+1] for global row g from one Philox draw (Box-Muller).
+// FP64 storage evaluates the transform in FP64; BF16 storage in FP32 (the result is
+// rounded to BF16 anyway).
+template <class TB>
+__device__ __forceinline__ void omega_pair(int64_t g, int p, uint64_t seed, double* z0, double* z1) {
+  uint32_t c[4] = {(uint32_t)g, (uint32_t)p, OMEGA_STREAM, 0u};
   philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-  const double u1 = unit53(c[0], c[1]);
-  const double u2 = unit53(c[2], c[3]);
-  const double r = sqrt(-2.0 * log(u1));
-  double sn, cs;
-  sincos(2.0 * 3.14159265358979323846 * u2, &sn, &cs);
-  return (j & 1) ? r * sn : r * cs;
+  if constexpr (sizeof(TB) == 8) {
+    const double u1 = unit53(c[0], c[1]);
+    const double u2 = unit53(c[2], c[3]);
+    const double r = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincos(2.0 * 3.14159265358979323846 * u2, &sn, &cs);
+    *z0 = r * cs;
+    *z1 = r * sn;
+  } else {
+    const float u1 = (float)unit53(c[0], c[1]);
+    const float u2 = (float)unit53(c[2], c[3]);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    *z0 = (double)(r * cs);
+    *z1 = (double)(r * sn);
+  }
 }
 
 // Transposed basis St (lpad x Ktot): St[j, koff_b + i] = Omega[v0_b + i, j] for j < lb_b,
-// i < rows_b; every other entry (columns j >= lb, padding i) is zero.
+// i < rows_b; every other entry (columns j >= lb, padding i) is zero.  One thread per
+// (column pair, basis column).
 template <class TB>
 __global__ void k_omega(Blocks B, uint64_t seed, TB* __restrict__ St) {
-  const int64_t total = (int64_t)B.lpad * B.Ktot;
+  const int64_t total = (int64_t)(B.lpad / 2) * B.Ktot;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(q / B.Ktot);
+    const int p = (int)(q / B.Ktot);
     const int64_t col = q % B.Ktot;
     const int b = find_block(B.koff, B.nb, col);
     const int64_t i = col - B.koff[b];
-    double v = 0.0;
-    if (i < B.rows[b] && j < B.lb[b]) v = omega_entry(B.v0[b] + i, j, seed);
-    St[q] = from_double<TB>(v);
+    double z0 = 0.0, z1 = 0.0;
+    if (i < B.rows[b] && 2 * p < B.lb[b]) omega_pair<TB>(B.v0[b] + i, p, seed, &z0, &z1);
+    St[(int64_t)(2 * p) * B.Ktot + col] = from_double<TB>(z0);
+    St[(int64_t)(2 * p + 1) * B.Ktot + col] = from_double<TB>(2 * p + 1 < B.lb[b] ? z1 : 0.0);
   }
 }
 
@@ -236,46 +258,80 @@ k_block_gemm_f64(Blocks B, const int32_t* __restrict__ unit_block, const int32_t
 
 // ---------------------------------------------------------------------------
 // Per-block cross Gram G_b = X_b^T Y_b (lpad x lpad, FP64) of two row panels with
-// row stride lpad: one CTA per block, rows in tiles of 64; products in the panel type,
-// tile partial sums added into FP64 accumulators.
+// row stride lpad.  Each CTA takes one block and one range of GRAM_SPLIT rows and
+// writes a partial Gram; k_gram_reduce adds a block's partials in range order.  A
+// thread owns a TxT tile of the Gram (T = lpad/16): per row it reads T values of each
+// panel from shared memory and does T*T FMAs in the panel type; tile sums over 64 rows
+// are added into FP64 accumulators.
 // ---------------------------------------------------------------------------
+constexpr int GRAM_SPLIT = 1024;
+
 template <class T, int LPAD>
-__global__ void __launch_bounds__(256) k_gram(Blocks B, const T* __restrict__ X, const T* __restrict__ Y,
-                                               double* __restrict__ G) {
-  constexpr int TR = 64;
-  constexpr int NE = (LPAD * LPAD + 255) / 256;
+__global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, const T* __restrict__ X,
+                                                    const T* __restrict__ Y, double* __restrict__ Gpart) {
+  constexpr int TR = sizeof(T) == 8 ? 32 : 64;
+  constexpr int TT = LPAD / 16;
   __shared__ T sx[TR][LPAD];
   __shared__ T sy[TR][LPAD];
-  const int b = blockIdx.x;
+  const int b = blockIdx.x / max_splits, split = blockIdx.x % max_splits;
   const int rows = B.rows[b];
+  const int r_begin = split * GRAM_SPLIT;
+  double* out = Gpart + (int64_t)blockIdx.x * LPAD * LPAD;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (r_begin >= rows) return;
+  const int r_end = rows < r_begin + GRAM_SPLIT ? rows : r_begin + GRAM_SPLIT;
   const int64_t r0 = B.arow[b];
-  double acc[NE];
+  double acc[TT][TT];
 #pragma unroll
-  for (int e = 0; e < NE; ++e) acc[e] = 0.0;
-  for (int t0 = 0; t0 < rows; t0 += TR) {
-    const int nr = rows - t0 < TR ? rows - t0 : TR;
+  for (int a = 0; a < TT; ++a)
+#pragma unroll
+    for (int c = 0; c < TT; ++c) acc[a][c] = 0.0;
+  for (int t0 = r_begin; t0 < r_end; t0 += TR) {
+    const int nr = r_end - t0 < TR ? r_end - t0 : TR;
     for (int q = threadIdx.x; q < TR * LPAD; q += blockDim.x) {
       const int rr = q / LPAD, jj = q % LPAD;
       sx[rr][jj] = rr < nr ? X[(r0 + t0 + rr) * LPAD + jj] : T(0);
       sy[rr][jj] = rr < nr ? Y[(r0 + t0 + rr) * LPAD + jj] : T(0);
     }
     __syncthreads();
+    T part[TT][TT];
 #pragma unroll
-    for (int e = 0; e < NE; ++e) {
-      const int q = threadIdx.x + e * 256;
-      if (q < LPAD * LPAD) {
-        const int i = q / LPAD, j = q % LPAD;
-        T a = T(0);
-        for (int rr = 0; rr < TR; ++rr) a = fma(sx[rr][i], sy[rr][j], a);
-        acc[e] += (double)a;
-      }
+    for (int a = 0; a < TT; ++a)
+#pragma unroll
+      for (int c = 0; c < TT; ++c) part[a][c] = T(0);
+#pragma unroll 4
+    for (int rr = 0; rr < TR; ++rr) {
+      T xv[TT], yv[TT];
+#pragma unroll
+      for (int a = 0; a < TT; ++a) xv[a] = sx[rr][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < TT; ++c) yv[c] = sy[rr][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < TT; ++a)
+#pragma unroll
+        for (int c = 0; c < TT; ++c) part[a][c] = fma(xv[a], yv[c], part[a][c]);
     }
+#pragma unroll
+    for (int a = 0; a < TT; ++a)
+#pragma unroll
+      for (int c = 0; c < TT; ++c) acc[a][c] += (double)part[a][c];
     __syncthreads();
   }
 #pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    const int q = threadIdx.x + e * 256;
-    if (q < LPAD * LPAD) G[(int64_t)b * LPAD * LPAD + q] = acc[e];
+  for (int a = 0; a < TT; ++a)
+#pragma unroll
+    for (int c = 0; c < TT; ++c) out[(ty + 16 * a) * LPAD + tx + 16 * c] = acc[a][c];
+}
+
+// G[b] = sum of the block's partial Grams in range order
+template <int LPAD>
+__global__ void k_gram_reduce(Blocks B, int max_splits, const double* __restrict__ Gpart, double* __restrict__ G) {
+  const int b = blockIdx.x;
+  const int nsplit = (B.rows[b] + GRAM_SPLIT - 1) / GRAM_SPLIT;
+  for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += Gpart[((int64_t)b * max_splits + sp) * LPAD * LPAD + q];
+    G[(int64_t)b * LPAD * LPAD + q] = s;
   }
 }
 
@@ -371,9 +427,10 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
   if (threadIdx.x == 0 && s_ndead) atomicAdd(fail, 1);
 }
 
-// Q = Y Rinv row by row (one CTA per 64-row tile of a block); writes the row panel Qf
-// (row stride lpad) and, if St is given, the transposed basis St[j, koff + i] for the
-// next product.  TY: panel type of Y/Qf; TR: type of Rinv used in the product.
+// Q = Y Rinv row by row (one CTA per 128-row tile of a block, 32 rows at a time);
+// writes the row panel Qf (row stride lpad) and, if St is given, the transposed basis
+// St[j, koff + i] for the next product, staged in shared memory so that every St row
+// receives 32 consecutive elements.
 template <class T, class TB, int LPAD>
 __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __restrict__ unit_block,
                                                      const int32_t* __restrict__ unit_tile, int nunits,
@@ -382,7 +439,7 @@ __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __r
   constexpr int TR = 128;
   extern __shared__ uint8_t smraw[];
   T* sr = reinterpret_cast<T*>(smraw);             // LPAD x LPAD
-  T* sy = sr + LPAD * LPAD;                         // 32 x LPAD staging
+  T* sy = sr + LPAD * LPAD;                         // 32 x LPAD staging (input rows, then output rows)
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int b = unit_block[u];
     const int rows = B.rows[b];
@@ -392,22 +449,31 @@ __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __r
     for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x)
       sr[q] = (T)Rinv[(int64_t)b * LPAD * LPAD + q];
     __syncthreads();
-    // each thread: one row (of up to 128) per pass, LPAD/2 columns per half-warp pairing
-    for (int sub = 0; sub < TR; sub += 32) {
+    for (int sub = 0; sub < TR && i0 + sub < rows; sub += 32) {
       for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x) {
         const int rr = q / LPAD, jj = q % LPAD;
         sy[q] = (i0 + sub + rr < rows) ? Y[(r0 + sub + rr) * LPAD + jj] : T(0);
       }
       __syncthreads();
-      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x) {
+      T outv[(32 * LPAD + 255) / 256];
+      int cnt = 0;
+      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x, ++cnt) {
         const int rr = q / LPAD, j = q % LPAD;
         T a = T(0);
         if (j < lb)
           for (int i = 0; i <= j; ++i) a = fma(sy[rr * LPAD + i], sr[i * LPAD + j], a);
-        const int irow = i0 + sub + rr;
-        if (irow < rows) {
-          Qf[(r0 + sub + rr) * LPAD + j] = a;
-          if (St) St[(int64_t)j * B.Ktot + B.koff[b] + irow] = from_double<TB>((double)a);
+        outv[cnt] = a;
+        if (i0 + sub + rr < rows) Qf[(r0 + sub + rr) * LPAD + j] = a;
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x, ++cnt) sy[q] = outv[cnt];
+      __syncthreads();
+      if (St) {
+        const int64_t kb0 = B.koff[b] + i0 + sub;
+        for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x) {
+          const int j = q / 32, rr = q % 32;
+          if (i0 + sub + rr < rows) St[(int64_t)j * B.Ktot + kb0 + rr] = from_double<TB>((double)sy[rr * LPAD + j]);
         }
       }
       __syncthreads();
@@ -440,17 +506,35 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
     W[q] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  __shared__ double red_off[8], red_tot[8];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) {
+    {
       double off = 0.0, tot = 0.0;
-      for (int i = 0; i < lb; ++i)
-        for (int j = 0; j < lb; ++j) {
-          const double a = A[i * LPAD + j];
-          tot += a * a;
-          if (i != j) off += a * a;
+      for (int q = threadIdx.x; q < lb * lb; q += blockDim.x) {
+        const int i = q / lb, j = q % lb;
+        const double a = A[i * LPAD + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red_off[threadIdx.x >> 5] = off;
+        red_tot[threadIdx.x >> 5] = tot;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          a += red_off[w];
+          t += red_tot[w];
         }
-      off_s = off;
-      tot_s = tot;
+        off_s = a;
+        tot_s = t;
+      }
     }
     __syncthreads();
     if (!(off_s > 1e-30 * tot_s) || lb < 2) break;

@@ -19,23 +19,83 @@ namespace hgl {
 constexpr int OP_THREADS = 256;
 constexpr int OP_WARPS = OP_THREADS / 32;
 
+// Hyperedges are visited in decreasing size order (`order`).  The first `nheavy` of
+// them (more than HEAVY_ROW members) get one thread block each: the block's warps
+// split the member list and their partial sums are added in warp order through
+// shared memory.  The remaining blocks walk the light rows one warp per row.
 template <class TX, class TT, int LG, int NV>
 __global__ void __launch_bounds__(OP_THREADS)
 k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-            const double* __restrict__ s, const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx,
-            int c0, int cw, TT* __restrict__ Tp, int64_t ldt, const int32_t* __restrict__ run_flag) {
+            const int32_t* __restrict__ order, int64_t nheavy, const double* __restrict__ s,
+            const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx, int c0, int cw, TT* __restrict__ Tp,
+            int64_t ldt, const int32_t* __restrict__ run_flag) {
   if (run_flag && *run_flag == 0) return;
   using A = typename AccOf<TX>::type;
   constexpr int E = 16 / (int)sizeof(TX);
   constexpr int G = 32 / LG;
   constexpr int U = 2;
-  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  constexpr int TILE = LG * NV * E;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
   const TX* Xc = X + c0;
-  for (int64_t e = warp; e < m; e += nwarps) {
+  A acc[NV][E];
+  if (blockIdx.x < nheavy) {
+    __shared__ A red[OP_WARPS][TILE];
+    const int32_t e = order[blockIdx.x];
     const int64_t beg = __ldg(csc_ptr + e), end = __ldg(csc_ptr + e + 1);
-    A acc[NV][E];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int j = 0; j < E; ++j) acc[k][j] = A(0);
+    for (int64_t i = beg + wid * G + grp; i < end; i += OP_WARPS * G) {
+      const int32_t v = __ldg(csc_idx + i);
+      const A sv = (A)__ldg(s + v);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, TX, E>(Xc + (int64_t)v * ldx + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) acc[k][j] = fma(sv, x[j], acc[k][j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int off = LG; off < 32; off <<= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[k][j] += __shfl_xor_sync(0xffffffffu, acc[k][j], off);
+    if (grp == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) red[wid][(k * LG + l) * E + j] = acc[k][j];
+    __syncthreads();
+    if (wid == 0 && grp == 0) {
+      const A te = (A)__ldg(t + e);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A o[E];
+#pragma unroll
+          for (int j = 0; j < E; ++j) {
+            A sum = A(0);
+            for (int w = 0; w < OP_WARPS; ++w) sum += red[w][col + j];
+            o[j] = te * sum;
+          }
+          vstore<TT, A, E>(Tp + (int64_t)e * ldt + col, o, E);
+        }
+      }
+    }
+    return;
+  }
+  const int64_t warp = (((int64_t)blockIdx.x - nheavy) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (((int64_t)gridDim.x - nheavy) * blockDim.x) >> 5;
+  for (int64_t q = nheavy + warp; q < m; q += nwarps) {
+    const int32_t e = order[q];
+    const int64_t beg = __ldg(csc_ptr + e), end = __ldg(csc_ptr + e + 1);
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
@@ -90,7 +150,7 @@ k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
           A o[E];
 #pragma unroll
           for (int j = 0; j < E; ++j) o[j] = te * acc[k][j];
-          vstore<TT, A, E>(Tp + e * ldt + col, o, E);
+          vstore<TT, A, E>(Tp + (int64_t)e * ldt + col, o, E);
         }
       }
     }

@@ -8,10 +8,13 @@ namespace hgl {
 // Default chunk width in 16-byte vectors per row (512 bytes of X per row).
 inline int default_chunk_vecs() { return 32; }
 
+// Blocks of the hyperedge pass: one per heavy hyperedge, then enough for the light
+// rows (capped at 8 resident blocks per SM; warps stride over the remaining rows).
 inline int edge_grid(const hgl_graph* g) {
-  int64_t need = (g->m + OP_WARPS - 1) / OP_WARPS;
+  const int64_t light = g->m - g->nheavy;
+  int64_t need = (light + OP_WARPS - 1) / OP_WARPS;
   int64_t cap = (int64_t)g->num_sms * 8;
-  return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  return (int)(g->nheavy + (need < cap ? (need > 0 ? need : 1) : cap));
 }
 
 inline int vertex_grid(const hgl_graph* g) {
@@ -55,7 +58,8 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
     const int cw = cl.c - c0 < cc ? cl.c - c0 : cc;
 #define HGL_EDGE_CASE(LG_, NV_)                                                                       \
   else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_edge_pass<TX, TT, LG_, NV_><<<grid1, OP_THREADS, 0, st>>>(          \
-      g->m, g->csc_ptr, g->csc_idx, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);
+      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc,   \
+      cl.run_flag);
 #define HGL_VERTEX_CASE(LG_, NV_)                                                                     \
   else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
       g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \

@@ -20,26 +20,34 @@ namespace hgl {
 
 namespace {
 
+// Heavy hyperedges (the first nheavy of `order`) get one block each, the others one
+// warp each, longest first.
 template <class TX, int LG, int NV, bool DUAL>
 __global__ void __launch_bounds__(OP_THREADS)
 k_grad_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-            const double* __restrict__ s, const double* __restrict__ t, const TX* __restrict__ F,
-            const TX* __restrict__ Zb, int64_t ld, int c0, int cw, typename AccOf<TX>::type* __restrict__ TF,
-            typename AccOf<TX>::type* __restrict__ TZ, int64_t ldt, double* __restrict__ ex) {
+            const int32_t* __restrict__ order, int64_t nheavy, const double* __restrict__ s,
+            const double* __restrict__ t, const TX* __restrict__ F, const TX* __restrict__ Zb, int64_t ld, int c0,
+            int cw, typename AccOf<TX>::type* __restrict__ TF, typename AccOf<TX>::type* __restrict__ TZ, int64_t ldt,
+            double* __restrict__ ex) {
   using A = typename AccOf<TX>::type;
   constexpr int E = 16 / (int)sizeof(TX);
   constexpr int G = 32 / LG;
-  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = warp; e < m; e += nwarps) {
+  constexpr int TILE = LG * NV * E;
+  const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
+  const bool heavy = blockIdx.x < nheavy;
+  const int64_t warp = heavy ? 0 : (((int64_t)blockIdx.x - nheavy) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = heavy ? 1 : (((int64_t)gridDim.x - nheavy) * blockDim.x) >> 5;
+  for (int64_t q = heavy ? blockIdx.x : nheavy + warp; q < (heavy ? (int64_t)blockIdx.x + 1 : m); q += nwarps) {
+    const int32_t e = order[q];
     const int64_t beg = csc_ptr[e], end = csc_ptr[e + 1];
     A sf[NV][E], sz[NV][E];
 #pragma unroll
     for (int k = 0; k < NV; ++k)
 #pragma unroll
       for (int j = 0; j < E; ++j) sf[k][j] = sz[k][j] = A(0);
-    for (int64_t i = beg + grp; i < end; i += G) {
+    const int64_t first = heavy ? beg + wid * G + grp : beg + grp;
+    const int64_t step = heavy ? (int64_t)OP_WARPS * G : G;
+    for (int64_t i = first; i < end; i += step) {
       const int32_t v = __ldg(csc_idx + i);
       const A sv = (A)__ldg(s + v);
 #pragma unroll
@@ -67,6 +75,32 @@ k_grad_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
           sf[k][j] += __shfl_xor_sync(0xffffffffu, sf[k][j], off);
           if (DUAL) sz[k][j] += __shfl_xor_sync(0xffffffffu, sz[k][j], off);
         }
+    if (heavy) {
+      __shared__ A red_f[OP_WARPS][TILE];
+      __shared__ A red_z[DUAL ? OP_WARPS : 1][DUAL ? TILE : 1];
+      if (grp == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+          for (int j = 0; j < E; ++j) {
+            red_f[wid][(k * LG + l) * E + j] = sf[k][j];
+            if (DUAL) red_z[wid][(k * LG + l) * E + j] = sz[k][j];
+          }
+      __syncthreads();
+      if (wid != 0) return;
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+          A a = A(0), b = A(0);
+          for (int w = 0; w < OP_WARPS; ++w) {
+            a += red_f[w][(k * LG + l) * E + j];
+            if (DUAL) b += red_z[w][(k * LG + l) * E + j];
+          }
+          sf[k][j] = a;
+          sz[k][j] = b;
+        }
+    }
     double d = 0.0;
     const A te = (A)t[e];
 #pragma unroll
@@ -210,13 +244,15 @@ hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld
   double* phi = vecs + g->m;
   const int64_t cap = (int64_t)g->num_sms * 8;
   const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + OP_WARPS - 1) / OP_WARPS, cap));
+  const int grid1h =
+      (int)(g->nheavy + std::max<int64_t>(1, std::min<int64_t>((g->m - g->nheavy + OP_WARPS - 1) / OP_WARPS, cap)));
   const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + OP_WARPS - 1) / OP_WARPS, cap));
   ProfScope prof(HGL_PROF_GRADIENT, st);
   for (int c0 = 0; c0 < c; c0 += cc) {
     const int cw = std::min(cc, c - c0);
 #define HGL_GE(LG_, NV_)                                                                                        \
-  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_edge<TX, LG_, NV_, DUAL><<<grid1, OP_THREADS, 0, st>>>(                 \
-      g->m, g->csc_ptr, g->csc_idx, g->s, g->t, F, Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);
+  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_edge<TX, LG_, NV_, DUAL><<<grid1h, OP_THREADS, 0, st>>>(                \
+      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, F, Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);
 #define HGL_GV(LG_, NV_)                                                                                        \
   else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_vertex<TX, LG_, NV_, DUAL><<<grid2, OP_THREADS, 0, st>>>(               \
       g->n, g->csr_ptr, g->csr_idx, g->s, TF, TZ, (int64_t)cc, F, Zb, ld, c0, cw, phi);
