@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--eta", type=float, default=None, help="override the workload's step size")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default column chunks (no autotuning)")
     return ap.parse_args()
 
 
@@ -278,7 +279,14 @@ def main():
     w = w0.clone()
     F = hgl.padded_panel(n, c, torch.float64, dev)
     stream = torch.cuda.current_stream()
-    counter = {"i": 0}
+    tuned = None
+    if not args.no_tune:
+        # pick the column chunks of the gather passes on this graph (untimed setup)
+        t0 = time.time()
+        op32, pair32 = hgl.tune_operator(g, w0, c, hgl.HGL_FP32)
+        op64, _ = hgl.tune_operator(g, w0, c, hgl.HGL_FP64)
+        tuned = {"operator_chunk_fp32": op32, "residual_chunk": pair32, "operator_chunk_fp64": op64,
+                 "tune_s": time.time() - t0}
 
     def reset():
         w.copy_(w0)
@@ -326,16 +334,18 @@ def main():
     value = world * args.steps / (ms / 1000.0)
     iters = [s.solve.iters for s in stats]
     relres_max = max(s.solve.relres_max for s in stats)
+    # ||w_new - w_old|| / ||w_old||, with ||w|| ~ 1/sqrt(m) near the uniform start
+    dw_rel = [s.dw_norm * float(np.sqrt(m)) for s in stats]
 
     # roofline of the dominant kernel family (event-timed inside the timed region)
     hbm_peak, bf16_peak, peak_kind = measured_peaks()
     kernel_names = {hgl.PROF_OPERATOR: "operator apply (k_edge_pass + k_vertex_pass), FP32 panels, c=512",
-                    hgl.PROF_RESIDUAL: "pair-arithmetic residual (df::k_edge + df::k_vertex), c=512 in 2 chunks",
+                    hgl.PROF_RESIDUAL: "pair-arithmetic residual (df::k_edge + df::k_vertex), c=512",
                     hgl.PROF_GEMM: "grouped block GEMM on tcgen05 (umma::k_block_gemm), BF16 in / FP32 out",
                     hgl.PROF_GRADIENT: "weight gradient (k_grad_edge + k_grad_vertex + k_grad_final), FP32"}
     lpad = ((K_RANK + P_OVER + 15) // 16) * 16
     per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4),
-                        hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, 2),
+                        hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, 1),
                         hgl.PROF_GEMM: bytes_gemm(bp, lpad),
                         hgl.PROF_GRADIENT: bytes_gradient(n, m, nnz, c)}
     families = {}
@@ -418,7 +428,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": dict(config_dict(d, bp), parallelism="replicas" if world > 1 else "single"),
-            "solve": {"cg_iters_per_step": iters, "relres_max": relres_max},
+            "solve": {"cg_iters_per_step": iters, "relres_max": relres_max,
+                      "dw_rel_to_uniform_w": dw_rel},
+            "tuned_chunks": tuned,
             "roofline": roofline,
             "kernel_families": families,
             "e2e": e2e,

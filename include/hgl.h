@@ -181,6 +181,26 @@ hgl_status hgl_apply_theta_noalloc(const hgl_graph* g, const double* w, double a
                                    const void* X, int64_t ldx, void* Z, int64_t ldz,
                                    int32_t c, hgl_dtype dtype, void* stream);
 
+/*
+ * hgl_tune_operator -- choose, by timing on this graph, the column chunk that the
+ * operator apply (Eq. 1) uses for c-column panels of `dtype`, and for FP32/BF16 also
+ * the chunk of the FP64-accurate pair residual that the mixed-precision solvers use.
+ * The paper has no counterpart: the chunk trades one long burst per gathered row
+ * against re-reading the index arrays once per chunk, and the best width depends on
+ * n, m, c, the panel type and the degree distribution.  The choice is stored in the
+ * graph and used by every later call with the same (dtype, c); untuned graphs use a
+ * fixed default.  Results of later calls may differ from untuned ones in summation
+ * order only (each column's sums are unchanged for the operator; the pair residual
+ * is FP64-accurate either way).  Allocates and frees temporary panels (3 n x c plus,
+ * for FP32/BF16, about 5 n x c floats).
+ *   w               device FP64[m] weights (sets the graph's degree vectors)
+ *   chunk_cols      optional host out: the chosen operator chunk in columns
+ *   pair_chunk_cols optional host out: the chosen residual chunk (0 for FP64)
+ * Synchronises `stream`.
+ */
+hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c, hgl_dtype dtype,
+                             int32_t* chunk_cols, int32_t* pair_chunk_cols, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Solve (Eq. 6 by conjugate gradient, Eqs. 16-20)                           */
 /* ------------------------------------------------------------------------- */

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 
 #include "../../include/hgl.h"
@@ -27,6 +28,11 @@ hgl_status record_error(hgl_status s, const char* fmt, ...);
 hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
 int device_sm_count();
+
+constexpr int TUNE_PAIR = 7;
+inline uint64_t tune_key(int kind, int c) { return ((uint64_t)kind << 32) | (uint32_t)c; }
+// Tuned chunk in vectors for (kind, c), or 0.
+inline int tuned_chunk_vecs(const hgl_graph* g, int kind, int c);
 
 // Rows (hyperedges) longer than this go to a whole thread block in the gather passes.
 constexpr int64_t HEAVY_ROW = 128;
@@ -80,6 +86,10 @@ struct hgl_graph {
   // processed by a whole thread block each, the rest by one warp each in this order
   int32_t* edge_order = nullptr;  // m
   int64_t nheavy = 0;
+  // column chunk (in 16-byte vectors per row) chosen by hgl_tune_operator, keyed by
+  // (panel kind, c); kind = HGL_FP64/FP32/BF16 for the operator, TUNE_PAIR for the
+  // pair-arithmetic residual
+  std::map<uint64_t, int> tuned_chunk;
 };
 
 #define HGL_CHECK_CUDA(call)                                                   \
@@ -151,3 +161,8 @@ int op_partial_rows(const hgl_graph* g);
 hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st);
 
 }  // namespace hgl
+
+inline int hgl::tuned_chunk_vecs(const hgl_graph* g, int kind, int c) {
+  auto it = g->tuned_chunk.find(tune_key(kind, c));
+  return it == g->tuned_chunk.end() ? 0 : it->second;
+}

@@ -30,7 +30,17 @@ __global__ void k_gains(int nb, int k, int lpad, const double* __restrict__ ev_i
 template <class T> struct AccT { using type = float; };
 template <> struct AccT<double> { using type = double; };
 
-// C[b, r, col] = gain[b, r] * sum_i Q[v0+i, r] R[v0+i, col]
+// Column chunk per CTA and rows per tile of the two kernels.  Threads form 8 rows of
+// 32 lanes; a thread owns KP/8 (projection) or 8 (expansion) output rows and
+// CW/32 columns, so every shared-memory load feeds several FMAs.
+template <class TP> struct ApplyShape {
+  static constexpr int CW = sizeof(TP) == 8 ? 64 : 128;
+  static constexpr int RT = 32;   // rows per tile in the projection
+  static constexpr int UR = 64;   // rows per expansion unit
+  static constexpr int KC = 16;   // rank rows of C staged at a time
+};
+
+// C[b, r, col] = gain[b, r] * sum_i Q[v0+i, r] R[v0+i, col]   (grid: blocks x column chunks)
 template <class TP, class TQ, int KP>
 __global__ void __launch_bounds__(256)
 k_precond_proj(int nb, const int64_t* __restrict__ v0, const int32_t* __restrict__ rows, const TQ* __restrict__ Q,
@@ -38,58 +48,60 @@ k_precond_proj(int nb, const int64_t* __restrict__ v0, const int32_t* __restrict
                typename AccT<TP>::type* __restrict__ C, const int32_t* __restrict__ run_flag) {
   if (run_flag && *run_flag == 0) return;
   using A = typename AccT<TP>::type;
-  constexpr int RT = 32;
-  __shared__ A sq[RT][KP + 1];
-  __shared__ A sr[RT][CW + 1];
+  using S = ApplyShape<TP>;
+  constexpr int CW = S::CW, RT = S::RT, NR = KP / 8, NC = CW / 32;
+  extern __shared__ __align__(16) uint8_t smraw[];
+  A* sq = reinterpret_cast<A*>(smraw);   // RT x KP
+  A* sr = sq + RT * KP;                  // RT x CW
   const int b = blockIdx.x;
   const int c0 = blockIdx.y * CW;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t base = v0[b];
   const int nrows = rows[b];
-  A acc[KP / 16][CW / 16];
+  A acc[NR][NC];
 #pragma unroll
-  for (int a = 0; a < KP / 16; ++a)
+  for (int a = 0; a < NR; ++a)
 #pragma unroll
-    for (int cc = 0; cc < CW / 16; ++cc) acc[a][cc] = A(0);
+    for (int cc = 0; cc < NC; ++cc) acc[a][cc] = A(0);
   for (int t0 = 0; t0 < nrows; t0 += RT) {
     for (int q = threadIdx.x; q < RT * KP; q += blockDim.x) {
       const int i = q / KP, r = q % KP;
-      sq[i][r] = (t0 + i < nrows && r < k) ? (A)Q[(base + t0 + i) * k + r] : A(0);
+      sq[q] = (t0 + i < nrows && r < k) ? (A)Q[(base + t0 + i) * k + r] : A(0);
     }
     for (int q = threadIdx.x; q < RT * CW; q += blockDim.x) {
       const int i = q / CW, j = q % CW;
-      sr[i][j] = (t0 + i < nrows && c0 + j < c) ? (A)R[(base + t0 + i) * ldr + c0 + j] : A(0);
+      sr[q] = (t0 + i < nrows && c0 + j < c) ? (A)R[(base + t0 + i) * ldr + c0 + j] : A(0);
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
     for (int i = 0; i < RT; ++i) {
-      A rv[CW / 16];
+      A rv[NC], qv[NR];
 #pragma unroll
-      for (int cc = 0; cc < CW / 16; ++cc) rv[cc] = sr[i][tx + 16 * cc];
+      for (int cc = 0; cc < NC; ++cc) rv[cc] = sr[i * CW + tx + 32 * cc];
 #pragma unroll
-      for (int a = 0; a < KP / 16; ++a) {
-        const A qv = sq[i][ty + 16 * a];
+      for (int a = 0; a < NR; ++a) qv[a] = sq[i * KP + ty * NR + a];
 #pragma unroll
-        for (int cc = 0; cc < CW / 16; ++cc) acc[a][cc] = fma(qv, rv[cc], acc[a][cc]);
-      }
+      for (int a = 0; a < NR; ++a)
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) acc[a][cc] = fma(qv[a], rv[cc], acc[a][cc]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int a = 0; a < KP / 16; ++a) {
-    const int r = ty + 16 * a;
+  for (int a = 0; a < NR; ++a) {
+    const int r = ty * NR + a;
     if (r < k) {
       const A gr = (A)gain[(int64_t)b * k + r];
 #pragma unroll
-      for (int cc = 0; cc < CW / 16; ++cc) {
-        const int col = c0 + tx + 16 * cc;
+      for (int cc = 0; cc < NC; ++cc) {
+        const int col = c0 + tx + 32 * cc;
         if (col < c) C[((int64_t)b * k + r) * c + col] = gr * acc[a][cc];
       }
     }
   }
 }
 
-// Z[rows of a 32-row tile] = R / (1+lam) + Q C_b  (C_b read in chunks of 16 rows)
+// Z = R / (1+lam) + Q C_b on one 64-row unit of a block and one column chunk
 template <class TP, class TQ, int KP>
 __global__ void __launch_bounds__(256)
 k_precond_expand(const int32_t* __restrict__ unit_block, const int32_t* __restrict__ unit_tile, int nunits,
@@ -98,53 +110,58 @@ k_precond_expand(const int32_t* __restrict__ unit_block, const int32_t* __restri
                  const typename AccT<TP>::type* __restrict__ C, const int32_t* __restrict__ run_flag) {
   if (run_flag && *run_flag == 0) return;
   using A = typename AccT<TP>::type;
-  constexpr int RT = 32, KC = 16;  // KC divides every padded rank KP (multiples of 16)
+  using S = ApplyShape<TP>;
+  constexpr int CW = S::CW, UR = S::UR, KC = S::KC, NR = UR / 8, NC = CW / 32;
   static_assert(KP % KC == 0, "rank chunk must divide the padded rank");
-  __shared__ A sq[RT][KP + 1];
-  __shared__ A sc[KC][CW + 1];
+  extern __shared__ __align__(16) uint8_t smraw[];
+  A* sq = reinterpret_cast<A*>(smraw);   // UR x (KP + 1)
+  A* sc = sq + UR * (KP + 1);             // KC x CW
   const int c0 = blockIdx.y * CW;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int b = unit_block[u];
-    const int i0 = unit_tile[u] * RT;
+    const int i0 = unit_tile[u] * UR;
     const int nrows = rows[b];
     const int64_t base = v0[b] + i0;
-    for (int q = threadIdx.x; q < RT * KP; q += blockDim.x) {
+    for (int q = threadIdx.x; q < UR * KP; q += blockDim.x) {
       const int i = q / KP, r = q % KP;
-      sq[i][r] = (i0 + i < nrows && r < k) ? (A)Q[(base + i) * k + r] : A(0);
+      sq[i * (KP + 1) + r] = (i0 + i < nrows && r < k) ? (A)Q[(base + i) * k + r] : A(0);
     }
-    A acc[2][CW / 16];
+    A acc[NR][NC];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < NR; ++a)
 #pragma unroll
-      for (int cc = 0; cc < CW / 16; ++cc) {
-        const int i = ty + 16 * a, col = c0 + tx + 16 * cc;
+      for (int cc = 0; cc < NC; ++cc) {
+        const int i = ty * NR + a, col = c0 + tx + 32 * cc;
         acc[a][cc] = (i0 + i < nrows && col < c) ? (A)R[(base + i) * ldr + col] * (A)inv1l : A(0);
       }
     for (int r0 = 0; r0 < KP; r0 += KC) {
       __syncthreads();
       for (int q = threadIdx.x; q < KC * CW; q += blockDim.x) {
         const int r = q / CW, j = q % CW;
-        sc[r][j] = (r0 + r < k && c0 + j < c) ? C[((int64_t)b * k + r0 + r) * c + c0 + j] : A(0);
+        sc[q] = (r0 + r < k && c0 + j < c) ? C[((int64_t)b * k + r0 + r) * c + c0 + j] : A(0);
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int r = 0; r < KC; ++r) {
+        A cv[NC];
 #pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const A qv = sq[ty + 16 * a][r0 + r];
+        for (int cc = 0; cc < NC; ++cc) cv[cc] = sc[r * CW + tx + 32 * cc];
 #pragma unroll
-          for (int cc = 0; cc < CW / 16; ++cc) acc[a][cc] = fma(qv, sc[r][tx + 16 * cc], acc[a][cc]);
+        for (int a = 0; a < NR; ++a) {
+          const A qv = sq[(ty * NR + a) * (KP + 1) + r0 + r];
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) acc[a][cc] = fma(qv, cv[cc], acc[a][cc]);
         }
       }
     }
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int i = ty + 16 * a;
+    for (int a = 0; a < NR; ++a) {
+      const int i = ty * NR + a;
       if (i0 + i < nrows)
 #pragma unroll
-        for (int cc = 0; cc < CW / 16; ++cc) {
-          const int col = c0 + tx + 16 * cc;
+        for (int cc = 0; cc < NC; ++cc) {
+          const int col = c0 + tx + 32 * cc;
           if (col < c) Z[(base + i) * ldz + col] = (TP)acc[a][cc];
         }
     }
@@ -156,24 +173,32 @@ template <class TP, class TQ>
 hgl_status apply_typed(hgl_precond* P, const TP* R, int64_t ldr, TP* Z, int64_t ldz, int c, cudaStream_t st,
                        const int32_t* run_flag) {
   using A = typename AccT<TP>::type;
+  using S = ApplyShape<TP>;
   ProfScope prof(HGL_PROF_PRECOND, st);
   hgl_status s = HGL_OK;
   A* C = static_cast<A*>(buffer_get(P->cbuf, sizeof(A) * (size_t)P->nb * P->k * c, &s));
   if (!C) return s;
   const int kp = (int)((P->k + 15) / 16 * 16);
   const int sms = device_sm_count();
-  dim3 g1(P->nb, (c + CW - 1) / CW);
-  dim3 g2(std::min(P->nunits, sms * 8), (c + CW - 1) / CW);
+  dim3 g1(P->nb, (c + S::CW - 1) / S::CW);
+  dim3 g2(std::min(P->nunits, sms * 8), (c + S::CW - 1) / S::CW);
   const TQ* Q = static_cast<const TQ*>(P->Q);
   const double inv1l = 1.0 / (1.0 + P->lam);
-#define HGL_KP_CASE(KPV)                                                                                              \
-  case KPV:                                                                                                           \
-    hgl::count_launch(2);                                                                                           \
-    k_precond_proj<TP, TQ, KPV><<<g1, 256, 0, st>>>(P->nb, P->d_v0, P->d_rows, Q, P->k, R, ldr, c, P->gain, C,        \
-                                                    run_flag);                                                        \
-    k_precond_expand<TP, TQ, KPV><<<g2, 256, 0, st>>>(P->unit_block, P->unit_tile, P->nunits, P->d_v0, P->d_rows, Q,  \
-                                                      P->k, R, ldr, Z, ldz, c, inv1l, C, run_flag);                   \
-    break;
+#define HGL_KP_CASE(KPV)                                                                                         \
+  case KPV: {                                                                                                    \
+    const size_t sm1 = sizeof(A) * (size_t)S::RT * (KPV + S::CW);                                                \
+    const size_t sm2 = sizeof(A) * ((size_t)S::UR * (KPV + 1) + (size_t)S::KC * S::CW);                          \
+    HGL_CHECK_CUDA(cudaFuncSetAttribute(k_precond_proj<TP, TQ, KPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)sm1));                                                              \
+    HGL_CHECK_CUDA(cudaFuncSetAttribute(k_precond_expand<TP, TQ, KPV>,                                           \
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));                 \
+    hgl::count_launch(2);                                                                                        \
+    k_precond_proj<TP, TQ, KPV><<<g1, 256, sm1, st>>>(P->nb, P->d_v0, P->d_rows, Q, P->k, R, ldr, c, P->gain, C, \
+                                                      run_flag);                                                 \
+    k_precond_expand<TP, TQ, KPV><<<g2, 256, sm2, st>>>(P->unit_block, P->unit_tile, P->nunits, P->d_v0,        \
+                                                        P->d_rows, Q, P->k, R, ldr, Z, ldz, c, inv1l, C,         \
+                                                        run_flag);                                               \
+  } break;
   switch (kp) {
     HGL_KP_CASE(16)
     HGL_KP_CASE(32)

@@ -20,7 +20,7 @@ struct hgl_precond {
   int64_t* d_v0 = nullptr;       // nb + 1 block boundaries
   int32_t* d_rows = nullptr;     // nb
   int32_t* d_kb = nullptr;       // nb
-  int32_t* unit_block = nullptr; // 32-row tiles used by the apply
+  int32_t* unit_block = nullptr; // 64-row units used by the apply
   int32_t* unit_tile = nullptr;
   int nunits = 0;
   hgl::Buffer cbuf;              // apply scratch: diag(g) Q^T R, nb x k x c

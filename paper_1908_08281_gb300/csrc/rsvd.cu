@@ -347,7 +347,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   P->kb = wk.kb;
   std::vector<int32_t> ub, ut;
   for (int b = 0; b < nb; ++b)
-    for (int t = 0; t < (wk.rows[b] + 31) / 32; ++t) {
+    for (int t = 0; t < (wk.rows[b] + 63) / 64; ++t) {  // 64-row units of the apply
       ub.push_back(b);
       ut.push_back(t);
     }

@@ -28,7 +28,8 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   hgl_graph* g = const_cast<hgl_graph*>(cl.g);
   constexpr int E = 16 / (int)sizeof(TX);
   const int nvec = (cl.c + E - 1) / E;
-  int chunk_vec = cl.chunk_cols > 0 ? (cl.chunk_cols + E - 1) / E : default_chunk_vecs();
+  const int tuned = tuned_chunk_vecs(g, cl.xdt, cl.c);
+  int chunk_vec = cl.chunk_cols > 0 ? (cl.chunk_cols + E - 1) / E : (tuned > 0 ? tuned : default_chunk_vecs());
   if (chunk_vec > nvec) chunk_vec = nvec;
   if (chunk_vec < 1) chunk_vec = 1;
   if (cl.scratch) {

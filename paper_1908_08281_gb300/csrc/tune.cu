@@ -1,0 +1,139 @@
+// tune.cu -- hgl_tune_operator: pick the column chunk of the gather passes by timing.
+//
+// The operator apply and the pair-arithmetic residual process the right-hand-side
+// columns in chunks; a wide chunk reads each gathered row in one long burst, a narrow
+// one keeps the gathered slice of the panel in L2 but re-reads the index arrays per
+// chunk.  Which wins depends on n, m, c, the panel type and the degree distribution,
+// so the chunk is chosen by timing every supported width on the graph itself.  The
+// choice is stored in the graph and used by later calls; untuned graphs use a fixed
+// default, so results never depend on timing unless the caller asks for tuning.
+#include <algorithm>
+
+#include "solver.cuh"
+#include "theta_launch.cuh"
+
+namespace hgl {
+namespace {
+
+struct DevMem {
+  void* p = nullptr;
+  ~DevMem() {
+    if (p) cudaFree(p);
+  }
+};
+
+template <class F>
+hgl_status time_ms(cudaStream_t st, F&& run, float* ms) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  HGL_CHECK_CUDA(cudaEventCreate(&a));
+  HGL_CHECK_CUDA(cudaEventCreate(&b));
+  hgl_status s = run();  // warm
+  if (s == HGL_OK) {
+    cudaEventRecord(a, st);
+    for (int r = 0; r < 2 && s == HGL_OK; ++r) s = run();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return s;
+}
+
+}  // namespace
+}  // namespace hgl
+
+extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c, hgl_dtype dtype,
+                                        int32_t* chunk_cols, int32_t* pair_chunk_cols, void* stream) {
+  using namespace hgl;
+  if (!g || !w) return record_error(HGL_ERR_INVALID_ARG, "graph or w is NULL");
+  if (c < 1) return record_error(HGL_ERR_INVALID_ARG, "c must be >= 1");
+  if (dtype != HGL_FP64 && dtype != HGL_FP32 && dtype != HGL_BF16)
+    return record_error(HGL_ERR_INVALID_ARG, "unknown dtype");
+  cudaStream_t st = as_stream(stream);
+  HGL_TRY(degrees_launch(g, w, st));
+  const size_t elt = dtype_size(dtype);
+  const int E = (int)(16 / elt);
+  const int64_t ld = (c + E - 1) / E * E;
+  const int nvec = (c + E - 1) / E;
+  DevMem X, Z;
+  HGL_CHECK_CUDA(cudaMalloc(&X.p, elt * (size_t)g->n * ld));
+  HGL_CHECK_CUDA(cudaMalloc(&Z.p, elt * (size_t)g->n * ld));
+  HGL_CHECK_CUDA(cudaMemsetAsync(X.p, 0x3F, elt * (size_t)g->n * ld, st));  // finite, normal values
+
+  // operator apply: chunk widths of 8 .. 128 vectors per row (each a distinct tile)
+  int best = 0;
+  float best_ms = 0.f;
+  for (int vecs : {8, 16, 32, 64, 128}) {
+    const int cand = std::min(vecs, nvec);
+    OpCall cl{};
+    cl.g = g;
+    cl.xdt = dtype;
+    cl.zdt = dtype;
+    cl.X = X.p;
+    cl.ldx = ld;
+    cl.Z = Z.p;
+    cl.ldz = ld;
+    cl.c = c;
+    cl.a = 1.5;
+    cl.b = -1.0;
+    cl.epi = EPI_PLAIN;
+    cl.chunk_cols = cand * E;
+    float ms = 0.f;
+    HGL_TRY(time_ms(st, [&] { return op_launch(cl, st, nullptr); }, &ms));
+    if (best == 0 || ms < best_ms) {
+      best = cand;
+      best_ms = ms;
+    }
+    if (cand == nvec) break;
+  }
+  g->tuned_chunk[tune_key(dtype, c)] = best;
+  if (chunk_cols) *chunk_cols = best * E;
+
+  // pair-arithmetic residual (used by the FP32 / BF16 solvers): 4-float vectors
+  if (dtype != HGL_FP64) {
+    const int64_t ld32 = (c + 3) / 4 * 4, ld64 = (c + 1) / 2 * 2;
+    const int pvec = (c + 3) / 4;
+    DevMem Fh, Fl, Y, R, sc, part;
+    HGL_CHECK_CUDA(cudaMalloc(&Fh.p, 4 * (size_t)g->n * ld32));
+    HGL_CHECK_CUDA(cudaMalloc(&Fl.p, 4 * (size_t)g->n * ld32));
+    HGL_CHECK_CUDA(cudaMalloc(&R.p, 4 * (size_t)g->n * ld32));
+    HGL_CHECK_CUDA(cudaMalloc(&Y.p, 8 * (size_t)g->n * ld64));
+    HGL_CHECK_CUDA(cudaMalloc(&sc.p, 4 * 2 * (size_t)(g->n + g->m)));
+    const int rows = std::max(op_partial_rows(g), g->num_sms * 8);
+    HGL_CHECK_CUDA(cudaMalloc(&part.p, 8 * (size_t)rows * c));
+    HGL_CHECK_CUDA(cudaMemsetAsync(Fh.p, 0x3F, 4 * (size_t)g->n * ld32, st));
+    HGL_CHECK_CUDA(cudaMemsetAsync(Fl.p, 0, 4 * (size_t)g->n * ld32, st));
+    HGL_CHECK_CUDA(cudaMemsetAsync(Y.p, 0, 8 * (size_t)g->n * ld64, st));
+    float* s_hi = static_cast<float*>(sc.p);
+    float* s_lo = s_hi + g->n;
+    float* t_hi = s_lo + g->n;
+    float* t_lo = t_hi + g->m;
+    HGL_TRY(df_split_scalings(g, s_hi, s_lo, t_hi, t_lo, st));
+    int pbest = 0;
+    float pbest_ms = 0.f;
+    const uint64_t key = tune_key(TUNE_PAIR, c);
+    for (int vecs : {8, 16, 32, 64}) {
+      const int cand = std::min(vecs, pvec);
+      g->tuned_chunk[key] = cand;
+      float ms = 0.f;
+      int r_rows = 0;
+      HGL_TRY(time_ms(st, [&] {
+        return df_residual(g, s_hi, s_lo, t_hi, t_lo, static_cast<float*>(Fh.p), static_cast<float*>(Fl.p), ld32,
+                           static_cast<double*>(Y.p), ld64, -1.5, 1.0, 0.5, c, static_cast<float*>(R.p),
+                           static_cast<double*>(part.p), st, &r_rows);
+      }, &ms));
+      if (pbest == 0 || ms < pbest_ms) {
+        pbest = cand;
+        pbest_ms = ms;
+      }
+      if (cand == pvec) break;
+    }
+    g->tuned_chunk[key] = pbest;
+    if (pair_chunk_cols) *pair_chunk_cols = pbest * 4;
+  } else if (pair_chunk_cols) {
+    *pair_chunk_cols = 0;
+  }
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  return HGL_OK;
+}

@@ -78,6 +78,7 @@ _SIGNATURES = {
     "hgl_degrees": (_I32, [_P, _P, _P, _P, _P, _P]),
     "hgl_apply_theta": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_apply_theta_noalloc": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
+    "hgl_tune_operator": (_I32, [_P, _P, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
     "hgl_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P, _P,
                             ctypes.POINTER(SolveStats), _P]),
     "hgl_block_rsvd": (_I32, [_P, _P, _D, ctypes.POINTER(_I64), _I32, _I32, _I32, _I32, _U64, _I32, _P,
@@ -294,6 +295,17 @@ def apply_theta_noalloc(g: Graph, w: torch.Tensor, X: torch.Tensor, Z: torch.Ten
         raise ValueError("X and Z must have the same dtype")
     _check(lib().hgl_apply_theta_noalloc(g.handle, _vec(w, "w"), a, b, px, ldx, pz, ldz, c, dt, _stream(stream)))
     return Z
+
+
+def tune_operator(g: Graph, w: torch.Tensor, c: int, dtype: int = HGL_FP64, stream=None) -> tuple[int, int]:
+    """Time the supported column chunks of the operator (and, for FP32/BF16, of the
+    pair residual) on this graph for c-column panels; the graph keeps the fastest.
+    Returns (operator chunk, residual chunk) in columns."""
+    op = ctypes.c_int32(0)
+    pair = ctypes.c_int32(0)
+    _check(lib().hgl_tune_operator(g.handle, _vec(w, "w"), c, dtype, ctypes.byref(op), ctypes.byref(pair),
+                                   _stream(stream)))
+    return op.value, pair.value
 
 
 def cg_solve(g: Graph, w: torch.Tensor, lam: float, Y: torch.Tensor, F: torch.Tensor | None = None,

@@ -142,6 +142,38 @@ def test_apply_theta_low_precision(dtype, rtol, c):
     assert (err <= rtol * scale + 1e-30).all(), err.max()
 
 
+@pytest.mark.parametrize("dtype,ch", [(hgl.HGL_FP64, torch.float64), (hgl.HGL_FP32, torch.float32)])
+def test_tuned_operator_and_residual_still_match(dtype, ch):
+    """Tuning only changes the column chunk: results stay within each path's bound."""
+    wl, d, og, H = _case("mixed_cg", 9, n=6000, m=9000, c=150)
+    c = d["c"]
+    rng = np.random.default_rng(11)
+    w = rng.random(d["m"]) + 0.01
+    w /= w.sum()
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    wt = torch.tensor(w, device=DEV)
+    op_cc, pair_cc = hgl.tune_operator(g, wt, c, dtype)
+    E = 16 // torch.tensor([], dtype=ch).element_size()
+    assert 1 <= op_cc and (op_cc % E == 0 or op_cc >= c)
+    if dtype == hgl.HGL_FP64:
+        assert pair_cc == 0
+    else:
+        assert pair_cc >= 4 and pair_cc % 4 == 0
+    Xt = _panel(rng.standard_normal((d["n"], c)), ch)
+    X = Xt.to(torch.float64).cpu().numpy()
+    Z = hgl.apply_theta(g, wt, Xt, 1.5, -1.0)
+    ref = core.theta_apply(H, w, X, 1.5, -1.0)
+    scale = np.abs(ref) + np.abs(1.5 * X) + core.theta_apply(H, w, np.abs(X), 0.0, 1.0)
+    rtol = 1e-13 if dtype == hgl.HGL_FP64 else 2e-6
+    assert (np.abs(Z.to(torch.float64).cpu().numpy() - ref) <= rtol * scale + 1e-30).all()
+    # the mixed solver uses the tuned residual chunk and still certifies its tolerance
+    Y = _panel(d["Y"])
+    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=1e-8, dtype=hgl.HGL_FP32)
+    refF, _ = core.certified_solve(H, w, wl.lam, d["Y"])
+    assert st.relres_max <= 1e-8
+    assert _relcol(F.cpu().numpy(), refF).max() <= (1 + wl.lam) / wl.lam * 1e-8 * 1.01 + 1e-12
+
+
 # ------------------------------------------------------------------------ CG ---
 
 def test_cg_fp64_small_workload():
