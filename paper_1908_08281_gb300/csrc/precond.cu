@@ -1,8 +1,8 @@
 // precond.cu -- the block preconditioner built by hgl_block_rsvd (Section 3, Eq. 15):
 //   z_b = r_b / (1+lam) + Q_b diag(g_b) Q_b^T r_b,   g = ev / ((1+lam)(1+lam-ev)),
-// applied block by block to an n x c panel: C_b = diag(g_b) Q_b^T R_b (k x c, reduced
-// over the block's rows by one CTA per block and column chunk), then
-// Z_b = R_b/(1+lam) + Q_b C_b (one CTA per 32-row tile and column chunk).
+// applied block by block to an n x c panel: C_b = diag(g_b) Q_b^T R_b (k x c), then
+// Z_b = R_b/(1+lam) + Q_b C_b.  FP32 panels with FP32 factors take the register-tiled
+// kernels below (k_pc_*); FP64 panels or factors take the generic pair k_precond_*.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -13,8 +13,6 @@
 
 namespace hgl {
 namespace {
-
-constexpr int CW = 64;  // columns per CTA
 
 __global__ void k_gains(int nb, int k, int lpad, const double* __restrict__ ev_in, const int32_t* __restrict__ kb,
                         double lam, double* __restrict__ ev_out, double* __restrict__ gain) {
@@ -169,6 +167,242 @@ k_precond_expand(const int32_t* __restrict__ unit_block, const int32_t* __restri
   }
 }
 
+// ---------------------------------------------------------------------------------
+// FP32 panels with FP32 factors (the mixed-precision solvers), rank k <= 64, k % 4 == 0.
+// Both contractions are register-tiled on the FP32 pipes: every thread owns an 8 x 8
+// output tile fed by two float4 shared-memory loads per operand and step, so each
+// step issues 64 FMAs per 4 shared loads.
+//   projection: one CTA per (slab of <= PC_SLAB block rows, 128 columns) writes the
+//               slab's 64 x 128 partial of Q_b^T R_b (double-buffered cp.async staging);
+//   reduction:  C_b = diag(g_b) (sum of the block's slab partials, in slab order);
+//   expansion:  one CTA per (128-row tile, 128 columns): Z = R/(1+lam) + Q_b C_b.
+// Summation orders are fixed, so results are reproducible run to run.
+constexpr int PF_R = 64;    // padded rank
+constexpr int PF_C = 128;   // columns per CTA
+constexpr int PF_RT = 32;   // block rows per staged projection step
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fma_8x8(float (&acc)[8][8], const float4& a0, const float4& a1, const float4& b0,
+                                        const float4& b1) {
+  const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+  const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+}
+
+// part[(slab * 64 + r) * ldp + col] = sum over the slab's rows i of Q[i, r] R[i, col]
+__global__ void __launch_bounds__(128)
+k_pc_proj_f32(const int32_t* __restrict__ slab_block, const int32_t* __restrict__ slab_row0,
+              const int64_t* __restrict__ v0, const int32_t* __restrict__ rows, const float* __restrict__ Q, int k,
+              const float* __restrict__ R, int64_t ldr, int c, float* __restrict__ part, int64_t ldp,
+              const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
+  __shared__ __align__(16) float sr[2][PF_RT][PF_C];   // 32 KB
+  __shared__ __align__(16) float sq[2][PF_RT][PF_R];   // 16 KB
+  const int slab = blockIdx.x;
+  const int b = slab_block[slab];
+  const int r0 = slab_row0[slab];
+  const int nrows = min(PC_SLAB, rows[b] - r0);
+  const int64_t base = v0[b] + r0;
+  const int c0 = blockIdx.y * PF_C;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // tx: columns, ty: ranks
+  auto stage = [&](int buf, int t0) {
+#pragma unroll
+    for (int q = tid; q < PF_RT * (PF_C / 4); q += 128) {
+      const int i = q >> 5, j = (q & 31) * 4;
+      const int row = t0 + i, col = c0 + j;
+      const float* src = R;
+      int bytes = 0;
+      if (row < nrows && col < c) {
+        src = R + (base + row) * ldr + col;
+        bytes = 4 * min(4, c - col);  // the rest of the 16 bytes is zero-filled
+      }
+      cp_async16(&sr[buf][i][j], src, bytes);
+    }
+#pragma unroll
+    for (int q = tid; q < PF_RT * (PF_R / 4); q += 128) {
+      const int i = q >> 4, r = (q & 15) * 4;
+      const int row = t0 + i;
+      const float* src = Q;
+      int bytes = 0;
+      if (row < nrows && r < k) {
+        src = Q + (base + row) * k + r;
+        bytes = 16;
+      }
+      cp_async16(&sq[buf][i][r], src, bytes);
+    }
+    cp_async_commit();
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const int nsteps = (nrows + PF_RT - 1) / PF_RT;
+  stage(0, 0);
+  for (int s = 0; s < nsteps; ++s) {
+    if (s + 1 < nsteps) {
+      stage((s + 1) & 1, (s + 1) * PF_RT);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int buf = s & 1;
+#pragma unroll 4
+    for (int i = 0; i < PF_RT; ++i) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&sq[buf][i][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&sq[buf][i][32 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&sr[buf][i][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&sr[buf][i][64 + tx * 4]);
+      fma_8x8(acc, a0, a1, b0, b1);
+    }
+    __syncthreads();
+  }
+  // columns c..ldp-1 hold zeros (zero-filled R), so whole float4 stores are safe
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = i < 4 ? ty * 4 + i : 32 + ty * 4 + (i - 4);
+    float* dst = part + ((int64_t)slab * PF_R + r) * ldp;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = c0 + h * 64 + tx * 4;
+      if (col < ldp)
+        *reinterpret_cast<float4*>(dst + col) =
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+    }
+  }
+}
+
+// C[(b * 64 + r) * ldp + col] = gain[b, r] * sum_{slabs of b, in order} part[...]
+__global__ void k_pc_reduce_f32(int nb, const int32_t* __restrict__ blk_slab0, const double* __restrict__ gain,
+                                int k, const float* __restrict__ part, int64_t ldp, float* __restrict__ C) {
+  const int64_t nvec = ldp / 4;
+  const int64_t total = (int64_t)nb * PF_R * nvec;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = q / nvec;  // b * 64 + r
+    const int col = (int)(q % nvec) * 4;
+    const int b = (int)(row / PF_R), r = (int)(row % PF_R);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int sl = blk_slab0[b]; sl < blk_slab0[b + 1]; ++sl) {
+      const float4 p = *reinterpret_cast<const float4*>(part + ((int64_t)sl * PF_R + r) * ldp + col);
+      s.x += p.x;
+      s.y += p.y;
+      s.z += p.z;
+      s.w += p.w;
+    }
+    const float g = r < k ? (float)gain[(int64_t)b * k + r] : 0.f;
+    *reinterpret_cast<float4*>(C + row * ldp + col) = make_float4(g * s.x, g * s.y, g * s.z, g * s.w);
+  }
+}
+
+// Z[rows of one 128-row tile, 128 columns] = R / (1+lam) + Q_b C_b
+__global__ void __launch_bounds__(256, 2)
+k_pc_expand_f32(const int32_t* __restrict__ exp_block, const int32_t* __restrict__ exp_tile,
+                const int64_t* __restrict__ v0, const int32_t* __restrict__ rows, const float* __restrict__ Q, int k,
+                const float* __restrict__ R, int64_t ldr, float* __restrict__ Z, int64_t ldz, int c, float inv1l,
+                const float* __restrict__ C, int64_t ldp, const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
+  extern __shared__ __align__(16) float smx[];
+  float* qt = smx;                  // [64 ranks][128 rows]  (Q tile transposed)
+  float* cs = smx + PF_R * PC_TILE;  // [64 ranks][128 columns]
+  const int u = blockIdx.x;
+  const int b = exp_block[u];
+  const int i0 = exp_tile[u] * PC_TILE;
+  const int nrows = rows[b];
+  const int64_t base = v0[b] + i0;
+  const int c0 = blockIdx.y * PF_C;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // tx: columns, ty: rows
+  const int kk = (k + 3) & ~3;
+  for (int q = tid; q < PC_TILE * (PF_R / 4); q += 256) {
+    const int i = q & (PC_TILE - 1), r = (q >> 7) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i0 + i < nrows && r < k) v = __ldg(reinterpret_cast<const float4*>(Q + (base + i) * k + r));
+    qt[(r + 0) * PC_TILE + i] = v.x;
+    qt[(r + 1) * PC_TILE + i] = v.y;
+    qt[(r + 2) * PC_TILE + i] = v.z;
+    qt[(r + 3) * PC_TILE + i] = v.w;
+  }
+  for (int q = tid; q < PF_R * (PF_C / 4); q += 256) {
+    const int r = q >> 5, j = (q & 31) * 4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c0 + j < ldp) v = __ldg(reinterpret_cast<const float4*>(C + ((int64_t)b * PF_R + r) * ldp + c0 + j));
+    *reinterpret_cast<float4*>(&cs[r * PF_C + j]) = v;
+  }
+  __syncthreads();
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+  for (int r = 0; r < kk; ++r) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&qt[r * PC_TILE + ty * 4]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&qt[r * PC_TILE + 64 + ty * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&cs[r * PF_C + tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&cs[r * PF_C + 64 + tx * 4]);
+    fma_8x8(acc, a0, a1, b0, b1);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+    if (i0 + row >= nrows) continue;
+    const float* rrow = R + (base + row) * ldr;
+    float* zrow = Z + (base + row) * ldz;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = c0 + h * 64 + tx * 4;
+      if (col + 3 < c) {
+        const float4 rv = __ldg(reinterpret_cast<const float4*>(rrow + col));
+        *reinterpret_cast<float4*>(zrow + col) =
+            make_float4(fmaf(inv1l, rv.x, acc[i][4 * h]), fmaf(inv1l, rv.y, acc[i][4 * h + 1]),
+                        fmaf(inv1l, rv.z, acc[i][4 * h + 2]), fmaf(inv1l, rv.w, acc[i][4 * h + 3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (col + j < c) zrow[col + j] = fmaf(inv1l, rrow[col + j], acc[i][4 * h + j]);
+      }
+    }
+  }
+}
+
+hgl_status apply_fast_f32(hgl_precond* P, const float* R, int64_t ldr, float* Z, int64_t ldz, int c, cudaStream_t st,
+                          const int32_t* run_flag) {
+  ProfScope prof(HGL_PROF_PRECOND, st);
+  const int64_t ldp = (c + 3) / 4 * 4;
+  hgl_status s = HGL_OK;
+  float* part = static_cast<float*>(buffer_get(P->pbuf, sizeof(float) * (size_t)P->nslabs * PF_R * ldp, &s));
+  if (!part) return s;
+  float* C = static_cast<float*>(buffer_get(P->cbuf, sizeof(float) * (size_t)P->nb * PF_R * ldp, &s));
+  if (!C) return s;
+  const int cchunks = (c + PF_C - 1) / PF_C;
+  const size_t sm_exp = sizeof(float) * 2 * PF_R * PC_TILE;
+  HGL_CHECK_CUDA(cudaFuncSetAttribute(k_pc_expand_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_exp));
+  hgl::count_launch(3);
+  k_pc_proj_f32<<<dim3(P->nslabs, cchunks), 128, 0, st>>>(P->slab_block, P->slab_row0, P->d_v0, P->d_rows,
+                                                          static_cast<const float*>(P->Q), P->k, R, ldr, c, part,
+                                                          ldp, run_flag);
+  const int64_t nred = (int64_t)P->nb * PF_R * (ldp / 4);
+  const int gred = (int)std::min<int64_t>((nred + 255) / 256, (int64_t)device_sm_count() * 8);
+  k_pc_reduce_f32<<<gred, 256, 0, st>>>(P->nb, P->blk_slab0, P->gain, P->k, part, ldp, C);
+  k_pc_expand_f32<<<dim3(P->nexp, cchunks), 256, sm_exp, st>>>(
+      P->exp_block, P->exp_tile, P->d_v0, P->d_rows, static_cast<const float*>(P->Q), P->k, R, ldr, Z, ldz, c,
+      (float)(1.0 / (1.0 + P->lam)), C, ldp, run_flag);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
 template <class TP, class TQ>
 hgl_status apply_typed(hgl_precond* P, const TP* R, int64_t ldr, TP* Z, int64_t ldz, int c, cudaStream_t st,
                        const int32_t* run_flag) {
@@ -247,7 +481,9 @@ hgl_status precond_apply_launch(const hgl_precond* Pc, const hgl_graph* g, const
     else
       HGL_TRY((apply_typed<double, double>(P, (const double*)R, ldr, (double*)Z, ldz, c, st, run_flag)));
   } else if (dt == HGL_FP32) {
-    if (f32q)
+    if (f32q && P->k <= PF_R && P->k % 4 == 0)
+      HGL_TRY(apply_fast_f32(P, (const float*)R, ldr, (float*)Z, ldz, c, st, run_flag));
+    else if (f32q)
       HGL_TRY((apply_typed<float, float>(P, (const float*)R, ldr, (float*)Z, ldz, c, st, run_flag)));
     else
       HGL_TRY((apply_typed<float, double>(P, (const float*)R, ldr, (float*)Z, ldz, c, st, run_flag)));
@@ -275,6 +511,7 @@ extern "C" void hgl_precond_destroy(hgl_precond* P) {
   if (!P) return;
   cudaFree(P->dev);
   hgl::buffer_free(P->cbuf);
+  hgl::buffer_free(P->pbuf);
   delete P;
 }
 

@@ -23,9 +23,21 @@ struct hgl_precond {
   int32_t* unit_block = nullptr; // 64-row units used by the apply
   int32_t* unit_tile = nullptr;
   int nunits = 0;
+  // FP32 apply: projection slabs (block, first row) of up to PC_SLAB rows, the first
+  // slab of every block (nb + 1 entries), and 128-row expansion tiles (block, tile)
+  int32_t* slab_block = nullptr;
+  int32_t* slab_row0 = nullptr;
+  int32_t* blk_slab0 = nullptr;
+  int nslabs = 0;
+  int32_t* exp_block = nullptr;
+  int32_t* exp_tile = nullptr;
+  int nexp = 0;
   hgl::Buffer cbuf;              // apply scratch: diag(g) Q^T R, nb x k x c
+  hgl::Buffer pbuf;              // FP32 apply scratch: per-slab partial projections
 };
 
 namespace hgl {
+constexpr int PC_SLAB = 2048;  // block rows reduced by one projection CTA
+constexpr int PC_TILE = 128;   // rows (and columns) of one expansion CTA
 hgl_status precond_gains_launch(hgl_precond* P, const double* ev_lpad, int lpad, cudaStream_t st);
 }  // namespace hgl

@@ -352,6 +352,21 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
       ut.push_back(t);
     }
   P->nunits = (int)ub.size();
+  std::vector<int32_t> sb, sr0, bs0, eb, et;
+  for (int b = 0; b < nb; ++b) {
+    bs0.push_back((int32_t)sb.size());
+    for (int r0 = 0; r0 < wk.rows[b]; r0 += PC_SLAB) {
+      sb.push_back(b);
+      sr0.push_back(r0);
+    }
+    for (int t = 0; t < (wk.rows[b] + PC_TILE - 1) / PC_TILE; ++t) {
+      eb.push_back(b);
+      et.push_back(t);
+    }
+  }
+  bs0.push_back((int32_t)sb.size());
+  P->nslabs = (int)sb.size();
+  P->nexp = (int)eb.size();
   const size_t eq = bf16 ? 4 : 8;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -367,6 +382,11 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   const size_t oKb = take(4 * (size_t)nb);
   const size_t oUb = take(4 * ub.size());
   const size_t oUt = take(4 * ut.size());
+  const size_t oSb = take(4 * sb.size());
+  const size_t oSr = take(4 * sr0.size());
+  const size_t oBs = take(4 * bs0.size());
+  const size_t oEb = take(4 * eb.size());
+  const size_t oEt = take(4 * et.size());
   cudaError_t e = cudaMalloc(&P->dev, off);
   if (e != cudaSuccess) {
     delete P;
@@ -381,6 +401,11 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   P->d_kb = reinterpret_cast<int32_t*>(base + oKb);
   P->unit_block = reinterpret_cast<int32_t*>(base + oUb);
   P->unit_tile = reinterpret_cast<int32_t*>(base + oUt);
+  P->slab_block = reinterpret_cast<int32_t*>(base + oSb);
+  P->slab_row0 = reinterpret_cast<int32_t*>(base + oSr);
+  P->blk_slab0 = reinterpret_cast<int32_t*>(base + oBs);
+  P->exp_block = reinterpret_cast<int32_t*>(base + oEb);
+  P->exp_tile = reinterpret_cast<int32_t*>(base + oEt);
   hgl_status fin = HGL_OK;
   auto chk = [&](cudaError_t ce) {
     if (ce != cudaSuccess && fin == HGL_OK) fin = cuda_error(ce, "preconditioner setup", __FILE__, __LINE__);
@@ -390,6 +415,11 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   chk(cudaMemcpyAsync(P->d_kb, wk.kb.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->unit_block, ub.data(), 4 * ub.size(), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->unit_tile, ut.data(), 4 * ut.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->slab_block, sb.data(), 4 * sb.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->slab_row0, sr0.data(), 4 * sr0.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->blk_slab0, bs0.data(), 4 * bs0.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->exp_block, eb.data(), 4 * eb.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->exp_tile, et.data(), 4 * et.size(), cudaMemcpyHostToDevice, st));
   const int nu = (int)wk.unit_block.size();
   if (fin == HGL_OK) {
     HGL_LPAD_SWITCH(lpad, {
