@@ -136,10 +136,11 @@ def make_inputs(scale: float):
 
 # ---- algorithmic bytes per launch of each kernel family (index + panels + vectors) ----
 
-def bytes_operator(n, m, nnz, c, elt):
-    """Operator apply Z = a X + b Theta X in one column chunk: indices once, X read by
-    both passes, the m x c intermediate written and read once, Z written once."""
-    return 2 * 4 * nnz + 8 * (n + m + 2) + 2 * n * c * elt + 2 * m * c * 4 + n * c * elt + 8 * (2 * n + m)
+def bytes_operator(n, m, nnz, c, elt, chunks=1):
+    """Operator apply Z = a X + b Theta X: per column chunk the indices; X read by both
+    passes, the m x c intermediate written and read once, Z written once."""
+    return chunks * (2 * 4 * nnz + 8 * (n + m + 2)) + 2 * n * c * elt + 2 * m * c * 4 + n * c * elt \
+        + 8 * (2 * n + m)
 
 
 def bytes_residual(n, m, nnz, c, chunks):
@@ -337,6 +338,18 @@ def main():
     # ||w_new - w_old|| / ||w_old||, with ||w|| ~ 1/sqrt(m) near the uniform start
     dw_rel = [s.dw_norm * float(np.sqrt(m)) for s in stats]
 
+    # accuracy (untimed): one more mixed-precision step, then the same system solved by
+    # FP64 CG to 1e-12 at that step's w; per-column relative error of the mixed F
+    w_in = w.clone()
+    step(F, w, args.steps, reset=False)
+    Fref = hgl.padded_panel(n, c, torch.float64, dev)
+    Fref.copy_(F)
+    _, _, _, st_ref = hgl.cg_solve(g, w_in, wl.lam, Y, F=Fref, tol=1e-12, max_iter=400, warm_start=True)
+    col_err = ((F - Fref).norm(dim=0) / Fref.norm(dim=0).clamp_min(1e-300)).max().item()
+    accuracy = {"max_col_rel_err_F_vs_fp64": col_err, "fp64_reference_relres": st_ref.relres_max,
+                "bound_from_tol": (1 + wl.lam) / wl.lam * TOL}
+    del Fref, w_in
+
     # roofline of the dominant kernel family (event-timed inside the timed region)
     hbm_peak, bf16_peak, peak_kind = measured_peaks()
     kernel_names = {hgl.PROF_OPERATOR: "operator apply (k_edge_pass + k_vertex_pass), FP32 panels, c=512",
@@ -344,8 +357,10 @@ def main():
                     hgl.PROF_GEMM: "grouped block GEMM on tcgen05 (umma::k_block_gemm), BF16 in / FP32 out",
                     hgl.PROF_GRADIENT: "weight gradient (k_grad_edge + k_grad_vertex + k_grad_final), FP32"}
     lpad = ((K_RANK + P_OVER + 15) // 16) * 16
-    per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4),
-                        hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, 1),
+    op_chunk = (tuned or {}).get("operator_chunk_fp32") or 128
+    pair_chunk = (tuned or {}).get("residual_chunk") or 256
+    per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4, -(-c // op_chunk)),
+                        hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, -(-c // pair_chunk)),
                         hgl.PROF_GEMM: bytes_gemm(bp, lpad),
                         hgl.PROF_GRADIENT: bytes_gradient(n, m, nnz, c)}
     families = {}
@@ -431,6 +446,7 @@ def main():
             "solve": {"cg_iters_per_step": iters, "relres_max": relres_max,
                       "dw_rel_to_uniform_w": dw_rel},
             "tuned_chunks": tuned,
+            "accuracy": accuracy,
             "roofline": roofline,
             "kernel_families": families,
             "e2e": e2e,

@@ -214,9 +214,10 @@ typedef struct {
   int32_t max_iter;    /* cap on CG iterations (all refinement sweeps together)          */
   int32_t dtype;       /* HGL_FP64: plain FP64 CG.  HGL_FP32 / HGL_BF16: CG on panels of */
                        /* that type with FP32 arithmetic, inside FP64 iterative          */
-                       /* refinement (residual recomputed in FP64 from the FP64 F)       */
-  double  inner_tol;   /* mixed modes: relative reduction asked of each inner solve      */
-                       /* (0 = 1e-4 for FP32, 1e-2 for BF16)                             */
+                       /* refinement (residual recomputed FP64-accurately from F)        */
+  double  inner_tol;   /* mixed modes: floor of the relative reduction asked of each     */
+                       /* inner solve; a sweep aims at max(inner_tol, 0.1 tol/relres)    */
+                       /* (0 = 1e-5 for FP32, 1e-2 for BF16)                             */
   int32_t max_refine;  /* mixed modes: cap on refinement sweeps (0 = 8)                  */
   int32_t flags;       /* HGL_SOLVE_WARM_START                                           */
 } hgl_solve_opts;

@@ -90,14 +90,16 @@ __global__ void k_set_target(CgState S, double tol2) {
 
 // Inner-solve targets of a refinement sweep: columns already at tol are frozen
 // (target +inf); the others aim at rr_inner <= rel^2 rr_true, rel = max(inner_tol,
-// 0.3 tol / relres) -- no more reduction than the outer tolerance still needs.
+// 0.1 tol / relres): ten times below what the outer tolerance still needs, so that
+// the FP32 rounding of the correction rarely forces another sweep (a sweep costs a
+// pair-arithmetic residual and a CG restart; the margin costs about one iteration).
 __global__ void k_inner_targets(CgState S, double tol, double inner_tol) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.c; j += gridDim.x * blockDim.x) {
     const double rel = S.relres[j];
     if (!(S.b2[j] > 0.0) || !(rel > tol) || !isfinite(rel)) {
       S.target[j] = INFINITY;
     } else {
-      double want = fmax(inner_tol, 0.3 * tol / rel);
+      double want = fmax(inner_tol, 0.1 * tol / rel);
       S.target[j] = want * want * S.rr[j];
     }
   }
@@ -388,7 +390,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   }
 
   // mixed precision: FP64 refinement around an FP32-arithmetic CG
-  const double inner_tol = o.inner_tol > 0 ? o.inner_tol : (mode == HGL_BF16 ? 1e-2 : 1e-4);
+  const double inner_tol = o.inner_tol > 0 ? o.inner_tol : (mode == HGL_BF16 ? 1e-2 : 1e-5);
   const int max_refine = o.max_refine > 0 ? o.max_refine : 8;
   float* R32 = static_cast<float*>(sm.R);
   float* X32 = static_cast<float*>(sm.X);

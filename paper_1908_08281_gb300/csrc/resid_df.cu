@@ -40,7 +40,7 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
   const int nvec = (c + E - 1) / E;
   int lg = 1, nv = 1;
   const int tuned = tuned_chunk_vecs(g, TUNE_PAIR, c);
-  pick_tile(std::min(nvec, tuned > 0 ? tuned : 64), &lg, &nv);
+  pick_tile(std::min(nvec, tuned > 0 ? tuned : 32), &lg, &nv);
   const int cc = lg * nv * E;
   hgl_status stt = HGL_OK;
   float* Th = static_cast<float*>(buffer_get(g->scratch, sizeof(float) * 2 * (size_t)g->m * cc, &stt));

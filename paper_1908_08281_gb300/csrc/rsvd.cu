@@ -248,7 +248,7 @@ hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool writ
   const int nu = (int)w.unit_block.size();
   const size_t chol_smem = 2 * sizeof(double) * LP * LP;
   HGL_TRY(set_smem(rsvd::k_chol_inv<LP>, chol_smem));
-  const size_t ap_smem = sizeof(T) * (LP * LP + 32 * LP);
+  const size_t ap_smem = sizeof(T) * (LP * LP + 128 * (LP + 1));
   HGL_TRY(set_smem(rsvd::k_apply_rinv<T, TB, LP>, ap_smem));
   // first pass: a small shift keeps the factorisation defined; both passes drop
   // pivots at the working precision's noise level (rank-deficient blocks)
@@ -324,9 +324,22 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
       hgl::count_launch();
       s_ = bf16 ? gram<float, LP>(wk, static_cast<const float*>(wk.Qf), static_cast<const float*>(wk.D), st)
                 : gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
-      const size_t jsm = 2 * sizeof(double) * LP * LP;
-      if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<LP>, jsm);
-      if (s_ == HGL_OK) { hgl::count_launch(); rsvd::k_jacobi<LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40); }
+      if (bf16) {
+        // FP32 rotations: the BF16 products bound the accuracy of T well above FP32's
+        const size_t jsm = 2 * sizeof(float) * LP * LP;
+        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<float, LP>, jsm);
+        if (s_ == HGL_OK) {
+          hgl::count_launch();
+          rsvd::k_jacobi<float, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 16, 1e-10);
+        }
+      } else {
+        const size_t jsm = 2 * sizeof(double) * LP * LP;
+        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
+        if (s_ == HGL_OK) {
+          hgl::count_launch();
+          rsvd::k_jacobi<double, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
+        }
+      }
     }
   });
   HGL_TRY(s_);
@@ -424,7 +437,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   if (fin == HGL_OK) {
     HGL_LPAD_SWITCH(lpad, {
       if (bf16) {
-        const size_t rs = sizeof(float) * LP * k;
+        const size_t rs = sizeof(float) * (LP * LP + 128 * (LP + 1));
         fin = set_smem(rsvd::k_ritz<float, LP>, rs);
         hgl::count_launch();
         if (fin == HGL_OK)
@@ -432,7 +445,7 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
               wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const float*>(wk.Qf), wk.R,
               static_cast<float*>(P->Q));
       } else {
-        const size_t rs = sizeof(double) * LP * k;
+        const size_t rs = sizeof(double) * (LP * LP + 128 * (LP + 1));
         fin = set_smem(rsvd::k_ritz<double, LP>, rs);
         hgl::count_launch();
         if (fin == HGL_OK)

@@ -96,13 +96,18 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
     if (lane == 0) row[i] = from_double<TA>(su * su * d);
     __syncwarp();
-    for (int64_t q = beg; q < end; ++q) {
-      const int32_t e = csr_idx[q];
-      const int64_t mb = csc_ptr[e], me = csc_ptr[e + 1];
-      // members of e inside [v0, v0 + bs): lower bounds by binary search (lane 0)
+    // off-diagonal terms: the lanes take 32 of u's hyperedges at a time and each finds
+    // the members of its hyperedge inside [v0, v0 + bs) by two binary searches over
+    // the sorted member list (independent searches, so their latencies overlap); the
+    // warp then adds the hyperedges that hold another block member, in CSR order.
+    for (int64_t q0 = beg; q0 < end; q0 += 32) {
+      const int64_t q = q0 + lane;
       int64_t lo = 0, hi = 0;
-      if (lane == 0) {
-        int64_t a = mb, z = me;
+      int32_t e = 0;
+      if (q < end) {
+        e = csr_idx[q];
+        int64_t a = csc_ptr[e], z = csc_ptr[e + 1];
+        const int64_t me = z;
         while (a < z) {
           const int64_t mid = (a + z) >> 1;
           if (csc_idx[mid] < v0) a = mid + 1; else z = mid;
@@ -115,19 +120,23 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
         }
         hi = a;
       }
-      lo = __shfl_sync(0xffffffffu, lo, 0);
-      hi = __shfl_sync(0xffffffffu, hi, 0);
-      if (hi - lo > 1) {
-        const double f = su * t[e];
-        for (int64_t p = lo + lane; p < hi; p += 32) {
+      unsigned todo = __ballot_sync(0xffffffffu, hi - lo > 1);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t l2 = __shfl_sync(0xffffffffu, lo, src);
+        const int64_t h2 = __shfl_sync(0xffffffffu, hi, src);
+        const int32_t e2 = __shfl_sync(0xffffffffu, e, src);
+        const double f = su * t[e2];
+        for (int64_t p = l2 + lane; p < h2; p += 32) {
           const int32_t v = csc_idx[p];
           if (v != u) {
             const int64_t j = v - v0;
             row[j] = from_double<TA>(to_double<TA>(row[j]) + f * s[v]);
           }
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
   }
 }
@@ -427,72 +436,92 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
   if (threadIdx.x == 0 && s_ndead) atomicAdd(fail, 1);
 }
 
-// Q = Y Rinv row by row (one CTA per 128-row tile of a block, 32 rows at a time);
-// writes the row panel Qf (row stride lpad) and, if St is given, the transposed basis
-// St[j, koff + i] for the next product, staged in shared memory so that every St row
-// receives 32 consecutive elements.
+// Q = Y Rinv on one 128-row tile of a block per CTA iteration.  A thread owns 8 rows x
+// LPAD/16 columns of the tile (rows tr + 16a, columns tc + 16c) and accumulates over
+// the block's lb basis columns from shared memory; Rinv is upper triangular (its
+// lower part is stored as zeros), so the sum over all i equals the sum over i <= j in
+// the same order.  The tile is staged with a row stride of LPAD + 1 words, which keeps
+// both the row products and the transposed St write free of bank conflicts.  Writes
+// the row panel Qf (row stride lpad; in place is fine, each tile reads its rows
+// before writing them) and, if St is given, the transposed basis St[j, koff + i].
 template <class T, class TB, int LPAD>
 __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __restrict__ unit_block,
                                                      const int32_t* __restrict__ unit_tile, int nunits,
-                                                     const T* __restrict__ Y, const double* __restrict__ Rinv,
-                                                     T* __restrict__ Qf, TB* __restrict__ St) {
-  constexpr int TR = 128;
-  extern __shared__ uint8_t smraw[];
-  T* sr = reinterpret_cast<T*>(smraw);             // LPAD x LPAD
-  T* sy = sr + LPAD * LPAD;                         // 32 x LPAD staging (input rows, then output rows)
+                                                     const T* Y, const double* __restrict__ Rinv, T* Qf,
+                                                     TB* __restrict__ St) {
+  constexpr int TR = 128, LS = LPAD + 1, CT = LPAD / 16, RT = TR / 16;
+  extern __shared__ __align__(16) uint8_t smraw[];
+  T* sr = reinterpret_cast<T*>(smraw);  // LPAD x LPAD
+  T* sy = sr + LPAD * LPAD;              // TR x LS
+  const int tc = threadIdx.x & 15, tr = threadIdx.x >> 4;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int b = unit_block[u];
     const int rows = B.rows[b];
     const int lb = B.lb[b];
-    const int64_t r0 = B.arow[b] + (int64_t)unit_tile[u] * TR;
     const int i0 = unit_tile[u] * TR;
-    for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x)
-      sr[q] = (T)Rinv[(int64_t)b * LPAD * LPAD + q];
-    __syncthreads();
-    for (int sub = 0; sub < TR && i0 + sub < rows; sub += 32) {
-      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x) {
-        const int rr = q / LPAD, jj = q % LPAD;
-        sy[q] = (i0 + sub + rr < rows) ? Y[(r0 + sub + rr) * LPAD + jj] : T(0);
-      }
-      __syncthreads();
-      T outv[(32 * LPAD + 255) / 256];
-      int cnt = 0;
-      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x, ++cnt) {
-        const int rr = q / LPAD, j = q % LPAD;
-        T a = T(0);
-        if (j < lb)
-          for (int i = 0; i <= j; ++i) a = fma(sy[rr * LPAD + i], sr[i * LPAD + j], a);
-        outv[cnt] = a;
-        if (i0 + sub + rr < rows) Qf[(r0 + sub + rr) * LPAD + j] = a;
-      }
-      __syncthreads();
-      cnt = 0;
-      for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x, ++cnt) sy[q] = outv[cnt];
-      __syncthreads();
-      if (St) {
-        const int64_t kb0 = B.koff[b] + i0 + sub;
-        for (int q = threadIdx.x; q < 32 * LPAD; q += blockDim.x) {
-          const int j = q / 32, rr = q % 32;
-          if (i0 + sub + rr < rows) St[(int64_t)j * B.Ktot + kb0 + rr] = from_double<TB>((double)sy[rr * LPAD + j]);
-        }
-      }
-      __syncthreads();
+    const int nr = rows - i0 < TR ? rows - i0 : TR;
+    const int64_t r0 = B.arow[b] + i0;
+    for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) sr[q] = (T)Rinv[(int64_t)b * LPAD * LPAD + q];
+    for (int q = threadIdx.x; q < TR * LPAD; q += blockDim.x) {
+      const int rr = q / LPAD, jj = q % LPAD;
+      sy[rr * LS + jj] = rr < nr ? Y[(r0 + rr) * LPAD + jj] : T(0);
     }
+    __syncthreads();
+    T acc[RT][CT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[a][c] = T(0);
+#pragma unroll 2
+    for (int i = 0; i < lb; ++i) {
+      T yv[RT], rv[CT];
+#pragma unroll
+      for (int a = 0; a < RT; ++a) yv[a] = sy[(tr + 16 * a) * LS + i];
+#pragma unroll
+      for (int c = 0; c < CT; ++c) rv[c] = sr[i * LPAD + tc + 16 * c];
+#pragma unroll
+      for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[a][c] = fma(yv[a], rv[c], acc[a][c]);
+    }
+    __syncthreads();  // every read of the input tile is done
+#pragma unroll
+    for (int a = 0; a < RT; ++a) {
+      const int row = tr + 16 * a;
+#pragma unroll
+      for (int c = 0; c < CT; ++c) {
+        const int col = tc + 16 * c;
+        sy[row * LS + col] = acc[a][c];
+        if (row < nr) Qf[(r0 + row) * LPAD + col] = acc[a][c];
+      }
+    }
+    __syncthreads();
+    if (St) {
+      const int64_t kb0 = B.koff[b] + i0;
+      for (int q = threadIdx.x; q < LPAD * TR; q += blockDim.x) {
+        const int j = q / TR, rr = q % TR;
+        if (rr < nr) St[(int64_t)j * B.Ktot + kb0 + rr] = from_double<TB>((double)sy[rr * LS + j]);
+      }
+    }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric eigendecomposition of T_b (lb x lb, FP64) by cyclic Jacobi with a
-// round-robin (tournament) ordering of disjoint pairs.  Writes the eigenvalues in
-// descending order and the matching eigenvectors (columns of V, LPAD x LPAD).
+// Symmetric eigendecomposition of T_b (lb x lb) by cyclic Jacobi with a round-robin
+// (tournament) ordering of disjoint pairs, in arithmetic type TJ (FP64 for the FP64
+// route; FP32 for the BF16 route, whose products are BF16-accurate anyway).  Sweeps
+// stop once the off-diagonal mass is below tol2 times the total.  Writes the
+// eigenvalues in descending order and the matching eigenvectors (columns of V,
+// LPAD x LPAD, FP64).
 // ---------------------------------------------------------------------------
-template <int LPAD>
+template <class TJ, int LPAD>
 __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restrict__ Tm, double* __restrict__ V,
-                                                 double* __restrict__ evals, int max_sweeps) {
-  extern __shared__ double sm[];
-  double* A = sm;                     // LPAD x LPAD
-  double* W = sm + LPAD * LPAD;       // eigenvectors
-  __shared__ double cs[LPAD / 2], sn[LPAD / 2];
+                                                 double* __restrict__ evals, int max_sweeps, double tol2) {
+  extern __shared__ __align__(16) uint8_t jsm_raw[];
+  TJ* A = reinterpret_cast<TJ*>(jsm_raw);   // LPAD x LPAD
+  TJ* W = A + LPAD * LPAD;                   // eigenvectors
+  __shared__ TJ cs[LPAD / 2], sn[LPAD / 2];
   __shared__ int pp[LPAD / 2], qq[LPAD / 2];
   __shared__ double off_s, tot_s;
   __shared__ int order[LPAD];
@@ -502,8 +531,8 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   const double* Tb = Tm + (int64_t)b * LPAD * LPAD;
   for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
     const int i = q / LPAD, j = q % LPAD;
-    A[q] = (i < lb && j < lb) ? 0.5 * (Tb[i * LPAD + j] + Tb[j * LPAD + i]) : 0.0;
-    W[q] = (i == j) ? 1.0 : 0.0;
+    A[q] = (i < lb && j < lb) ? (TJ)(0.5 * (Tb[i * LPAD + j] + Tb[j * LPAD + i])) : TJ(0);
+    W[q] = (i == j) ? TJ(1) : TJ(0);
   }
   __syncthreads();
   __shared__ double red_off[8], red_tot[8];
@@ -512,7 +541,7 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
       double off = 0.0, tot = 0.0;
       for (int q = threadIdx.x; q < lb * lb; q += blockDim.x) {
         const int i = q / lb, j = q % lb;
-        const double a = A[i * LPAD + j];
+        const double a = (double)A[i * LPAD + j];
         tot += a * a;
         if (i != j) off += a * a;
       }
@@ -537,7 +566,7 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
       }
     }
     __syncthreads();
-    if (!(off_s > 1e-30 * tot_s) || lb < 2) break;
+    if (!(off_s > tol2 * tot_s) || lb < 2) break;
     for (int round = 0; round < n - 1; ++round) {
       // tournament pairs: position 0 fixed, others rotate
       for (int p = threadIdx.x; p < n / 2; p += blockDim.x) {
@@ -550,14 +579,14 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
         }
         pp[p] = a;
         qq[p] = z;
-        double c = 1.0, s = 0.0;
+        TJ c = TJ(1), s = TJ(0);
         if (z < lb) {
-          const double apq = A[a * LPAD + z];
-          if (apq != 0.0) {
-            const double app = A[a * LPAD + a], aqq = A[z * LPAD + z];
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(tt * tt + 1.0);
+          const TJ apq = A[a * LPAD + z];
+          if (apq != TJ(0)) {
+            const TJ app = A[a * LPAD + a], aqq = A[z * LPAD + z];
+            const TJ theta = (aqq - app) / (TJ(2) * apq);
+            const TJ tt = (theta >= TJ(0) ? TJ(1) : TJ(-1)) / (fabs(theta) + sqrt(theta * theta + TJ(1)));
+            c = TJ(1) / sqrt(tt * tt + TJ(1));
             s = tt * c;
           }
         }
@@ -570,8 +599,8 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
         const int p = q / lb, col = q % lb;
         const int a = pp[p], z = qq[p];
         if (z < lb) {
-          const double c = cs[p], s = sn[p];
-          const double x = A[a * LPAD + col], y = A[z * LPAD + col];
+          const TJ c = cs[p], s = sn[p];
+          const TJ x = A[a * LPAD + col], y = A[z * LPAD + col];
           A[a * LPAD + col] = c * x - s * y;
           A[z * LPAD + col] = s * x + c * y;
         }
@@ -582,11 +611,11 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
         const int p = q / lb, row = q % lb;
         const int a = pp[p], z = qq[p];
         if (z < lb) {
-          const double c = cs[p], s = sn[p];
-          const double x = A[row * LPAD + a], y = A[row * LPAD + z];
+          const TJ c = cs[p], s = sn[p];
+          const TJ x = A[row * LPAD + a], y = A[row * LPAD + z];
           A[row * LPAD + a] = c * x - s * y;
           A[row * LPAD + z] = s * x + c * y;
-          const double vx = W[row * LPAD + a], vy = W[row * LPAD + z];
+          const TJ vx = W[row * LPAD + a], vy = W[row * LPAD + z];
           W[row * LPAD + a] = c * vx - s * vy;
           W[row * LPAD + z] = s * vx + c * vy;
         }
@@ -596,10 +625,10 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   }
   // sort eigenvalues descending (selection by rank; ties broken by index)
   for (int i = threadIdx.x; i < lb; i += blockDim.x) {
-    const double di = A[i * LPAD + i];
+    const TJ di = A[i * LPAD + i];
     int rank = 0;
     for (int j = 0; j < lb; ++j) {
-      const double dj = A[j * LPAD + j];
+      const TJ dj = A[j * LPAD + j];
       if (dj > di || (dj == di && j < i)) ++rank;
     }
     order[rank] = i;
@@ -608,40 +637,68 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   double* Vb = V + (int64_t)b * LPAD * LPAD;
   for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
     const int i = q / LPAD, r = q % LPAD;  // Vb[i, r] = W[i, order[r]]
-    Vb[q] = (r < lb && i < lb) ? W[i * LPAD + order[r]] : 0.0;
+    Vb[q] = (r < lb && i < lb) ? (double)W[i * LPAD + order[r]] : 0.0;
   }
   for (int r = threadIdx.x; r < LPAD; r += blockDim.x)
-    evals[(int64_t)b * LPAD + r] = r < lb ? A[order[r] * LPAD + order[r]] : 0.0;
+    evals[(int64_t)b * LPAD + r] = r < lb ? (double)A[order[r] * LPAD + order[r]] : 0.0;
 }
 
 // Ritz vectors: Qout[v0 + i, r] = sum_j S[i, j] V[j, r] for r < kb (row panel S with
-// stride lpad; output row stride k).  One CTA per 128-row tile.
+// stride lpad; output row stride k).  One 128-row tile per CTA iteration, register
+// tiled as k_apply_rinv (V staged zero-padded to LPAD x LPAD).
 template <class T, int LPAD>
 __global__ void __launch_bounds__(256) k_ritz(Blocks B, const int32_t* __restrict__ unit_block,
                                                const int32_t* __restrict__ unit_tile, int nunits,
                                                const T* __restrict__ S, const double* __restrict__ V,
                                                T* __restrict__ Qout) {
-  extern __shared__ uint8_t smraw[];
-  T* sv = reinterpret_cast<T*>(smraw);  // LPAD x k
+  constexpr int TR = 128, LS = LPAD + 1, CT = LPAD / 16, RT = TR / 16;
+  extern __shared__ __align__(16) uint8_t smraw[];
+  T* sv = reinterpret_cast<T*>(smraw);  // LPAD x LPAD
+  T* ss = sv + LPAD * LPAD;              // TR x LS
   const int k = B.k;
+  const int tc = threadIdx.x & 15, tr = threadIdx.x >> 4;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int b = unit_block[u];
     const int rows = B.rows[b];
     const int lb = B.lb[b], kb = B.kb[b];
-    const int i0 = unit_tile[u] * 128;
+    const int i0 = unit_tile[u] * TR;
+    const int nr = rows - i0 < TR ? rows - i0 : TR;
     const int64_t r0 = B.arow[b] + i0;
-    for (int q = threadIdx.x; q < LPAD * k; q += blockDim.x) {
-      const int j = q / k, r = q % k;
-      sv[q] = (j < lb && r < kb) ? (T)V[(int64_t)b * LPAD * LPAD + j * LPAD + r] : T(0);
+    for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
+      const int j = q / LPAD, r = q % LPAD;
+      sv[q] = (j < lb && r < kb) ? (T)V[(int64_t)b * LPAD * LPAD + q] : T(0);
+    }
+    for (int q = threadIdx.x; q < TR * LPAD; q += blockDim.x) {
+      const int rr = q / LPAD, jj = q % LPAD;
+      ss[rr * LS + jj] = rr < nr ? S[(r0 + rr) * LPAD + jj] : T(0);
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < 128 * k; q += blockDim.x) {
-      const int rr = q / k, r = q % k;
-      if (i0 + rr < rows) {
-        T a = T(0);
-        for (int j = 0; j < lb; ++j) a = fma(S[(r0 + rr) * LPAD + j], sv[j * k + r], a);
-        Qout[(B.v0[b] + i0 + rr) * k + r] = a;
-      }
+    T acc[RT][CT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[a][c] = T(0);
+#pragma unroll 2
+    for (int j = 0; j < lb; ++j) {
+      T sv_[CT], xv[RT];
+#pragma unroll
+      for (int a = 0; a < RT; ++a) xv[a] = ss[(tr + 16 * a) * LS + j];
+#pragma unroll
+      for (int c = 0; c < CT; ++c) sv_[c] = sv[j * LPAD + tc + 16 * c];
+#pragma unroll
+      for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[a][c] = fma(xv[a], sv_[c], acc[a][c]);
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a) {
+      const int row = tr + 16 * a;
+      if (row < nr)
+#pragma unroll
+        for (int c = 0; c < CT; ++c) {
+          const int r = tc + 16 * c;
+          if (r < k) Qout[(B.v0[b] + i0 + row) * k + r] = acc[a][c];
+        }
     }
     __syncthreads();
   }

@@ -80,8 +80,9 @@ def test_rsvd_bf16_tensor_cores_vs_fp64(k, p):
         e64, e16 = e64.cpu().numpy(), e16.cpu().numpy()
         q64, q16 = q64.cpu().numpy(), q16.cpu().numpy()
         worst = max(worst, np.abs(e64 - e16).max() / max(e64.max(), 1e-12))
-        # orthonormal Ritz vectors (FP32 CholeskyQR2 on FP32 products)
-        assert np.abs(q16.T @ q16 - np.eye(q16.shape[1])).max() <= 1e-5
+        # orthonormal Ritz vectors: FP32 CholeskyQR2 on FP32 products, then FP32 Jacobi
+        # rotations (about a thousand per column, each orthogonal to FP32 rounding)
+        assert np.abs(q16.T @ q16 - np.eye(q16.shape[1])).max() <= 3e-5
         if b < 8:
             # Ritz residual against the exact FP64 block: BF16 operands cost ~2^-8 relative
             Tb = blocks[b]
