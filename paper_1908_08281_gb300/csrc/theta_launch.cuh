@@ -65,14 +65,34 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
       g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
       cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
-    if (false) {
+#define HGL_EDGE_ROWS(LG_)                                                                            \
+  else if (lg == LG_) hgl::count_launch(), k_edge_rows<TX, TT, LG_><<<grid1, OP_THREADS, 0, st>>>(         \
+      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc,   \
+      cl.run_flag);
+#define HGL_VERTEX_ROWS(LG_)                                                                          \
+  else if (lg == LG_) hgl::count_launch(), k_vertex_rows<TX, TT, TZ, LG_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
+      g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
+      cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
+    if (nv == 1 && lg <= 8) {
+      // narrow chunk: one row per group of lanes
+      if (false) {
+      }
+      HGL_FOR_EACH_ROW_LG(HGL_EDGE_ROWS)
+      if (false) {
+      }
+      HGL_FOR_EACH_ROW_LG(HGL_VERTEX_ROWS)
+    } else {
+      if (false) {
+      }
+      HGL_FOR_EACH_WIDE_TILE(HGL_EDGE_CASE)
+      if (false) {
+      }
+      HGL_FOR_EACH_WIDE_TILE(HGL_VERTEX_CASE)
     }
-    HGL_FOR_EACH_TILE(HGL_EDGE_CASE)
-    if (false) {
-    }
-    HGL_FOR_EACH_TILE(HGL_VERTEX_CASE)
 #undef HGL_EDGE_CASE
 #undef HGL_VERTEX_CASE
+#undef HGL_EDGE_ROWS
+#undef HGL_VERTEX_ROWS
     HGL_CHECK_CUDA(cudaGetLastError());
   }
   if (grid2_out) *grid2_out = grid2;

@@ -61,10 +61,11 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
   HGL_CHECK_CUDA(cudaMalloc(&Z.p, elt * (size_t)g->n * ld));
   HGL_CHECK_CUDA(cudaMemsetAsync(X.p, 0x3F, elt * (size_t)g->n * ld, st));  // finite, normal values
 
-  // operator apply: chunk widths of 8 .. 128 vectors per row (each a distinct tile)
+  // operator apply: chunk widths of 1 .. 128 vectors per row (each a distinct tile;
+  // up to 8 vectors the row-per-group kernels, above them the member-parallel ones)
   int best = 0;
   float best_ms = 0.f;
-  for (int vecs : {8, 16, 32, 64, 128}) {
+  for (int vecs : {1, 2, 4, 8, 16, 32, 64, 128}) {
     const int cand = std::min(vecs, nvec);
     OpCall cl{};
     cl.g = g;

@@ -127,7 +127,7 @@ def test_apply_theta_fp64(c):
 
 
 @pytest.mark.parametrize("dtype,rtol", [(torch.float32, 2e-6), (torch.bfloat16, 1.2e-2)])
-@pytest.mark.parametrize("c", [5, 128, 200])
+@pytest.mark.parametrize("c", [5, 16, 30, 128, 200])
 def test_apply_theta_low_precision(dtype, rtol, c):
     _, d, og, H = _case("mixed_cg", 8, n=5000, m=8000, c=c)
     rng = np.random.default_rng(3)
