@@ -3,7 +3,9 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "hgl_internal.cuh"
@@ -115,6 +117,24 @@ void buffer_free(Buffer& b) {
   b.bytes = 0;
 }
 
+int resident_blocks(const void* fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, int, size_t>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const auto key = std::make_tuple(fn, dev, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) {
+    (void)cudaGetLastError();
+    nb = 1;
+  }
+  cache[key] = nb;
+  return nb;
+}
+
 int device_sm_count() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -126,21 +146,28 @@ int device_sm_count() {
 __global__ void k_degrees(int64_t n, int64_t m, const int64_t* __restrict__ csr_ptr,
                           const int32_t* __restrict__ csr_idx, const int32_t* __restrict__ de,
                           const double* __restrict__ w, double* __restrict__ dv,
-                          double* __restrict__ s, double* __restrict__ t) {
+                          double* __restrict__ s, double* __restrict__ t, float* __restrict__ s32,
+                          float* __restrict__ t32) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
     double acc = 0.0;
     for (int64_t i = csr_ptr[v], end = csr_ptr[v + 1]; i < end; ++i) acc += w[csr_idx[i]];
     dv[v] = acc;
-    s[v] = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+    const double sv = acc > 0.0 ? 1.0 / sqrt(acc) : 0.0;
+    s[v] = sv;
+    s32[v] = (float)sv;
   }
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride)
-    t[e] = w[e] / (double)de[e];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += stride) {
+    const double te = w[e] / (double)de[e];
+    t[e] = te;
+    t32[e] = (float)te;
+  }
 }
 
 hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st) {
   int blocks = g->num_sms * 8;
-  hgl::count_launch(); k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t);
+  hgl::count_launch(); k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t,
+                                                         g->s32, g->t32);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -205,6 +232,8 @@ void hgl_graph_destroy(hgl_graph* g) {
   cudaFree(g->dv);
   cudaFree(g->s);
   cudaFree(g->t);
+  cudaFree(g->s32);
+  cudaFree(g->t32);
   cudaFree(g->edge_order);
   hgl::buffer_free(g->scratch);
   hgl::buffer_free(g->scratch2);

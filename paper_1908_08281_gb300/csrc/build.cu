@@ -334,6 +334,8 @@ hgl_status build(int64_t n, int64_t m, const int64_t* edge_ptr, const int32_t* m
   HGL_CHECK_CUDA(cudaMalloc(&g->dv, sizeof(double) * n));
   HGL_CHECK_CUDA(cudaMalloc(&g->s, sizeof(double) * n));
   HGL_CHECK_CUDA(cudaMalloc(&g->t, sizeof(double) * m));
+  HGL_CHECK_CUDA(cudaMalloc(&g->s32, sizeof(float) * n));
+  HGL_CHECK_CUDA(cudaMalloc(&g->t32, sizeof(float) * m));
 
   // temporaries: bits | counts[2] | cnt[n] | cursor[n] | lists[max(n,m)] x2 | tile sums
   const int64_t nseg_max = n > m ? n : m;

@@ -29,6 +29,10 @@ hgl_status cuda_error(cudaError_t e, const char* what, const char* file, int lin
 
 int device_sm_count();
 
+// Blocks of kernel `fn` that fit on one SM at `threads` threads and `smem` bytes of
+// dynamic shared memory (occupancy API, cached per kernel and device; 1 on failure).
+int resident_blocks(const void* fn, int threads, size_t smem);
+
 constexpr int TUNE_PAIR = 7;
 inline uint64_t tune_key(int kind, int c) { return ((uint64_t)kind << 32) | (uint32_t)c; }
 // Tuned chunk in vectors for (kind, c), or 0.
@@ -74,6 +78,8 @@ struct hgl_graph {
   double* dv = nullptr;        // n   (for the w of the last degrees call)
   double* s = nullptr;         // n   dv^-1/2 (0 where dv <= 0)
   double* t = nullptr;         // m   w / de
+  float* s32 = nullptr;        // n   s rounded to FP32 (scalings of the FP32/BF16 kernels)
+  float* t32 = nullptr;        // m   t rounded to FP32
   hgl::Buffer scratch;         // m x chunk intermediate panel of the operator
   hgl::Buffer scratch2;        // second intermediate panel (bilinear gradient)
   hgl::Buffer partials;        // per-block reduction partials
@@ -160,6 +166,18 @@ int op_partial_rows(const hgl_graph* g);
 // Recompute dv, s, t for w into the graph's vectors.
 hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st);
 
+}  // namespace hgl
+
+namespace hgl {
+// The scalings s = dv^-1/2 and t = w/de in the accumulation type A of a kernel: FP64
+// kernels read the FP64 vectors, FP32 ones the FP32 copies (the same values the
+// kernels would get by rounding on every load, without an FP64 conversion per gather).
+template <class A> inline const A* scal_s(const hgl_graph* g);
+template <> inline const double* scal_s<double>(const hgl_graph* g) { return g->s; }
+template <> inline const float* scal_s<float>(const hgl_graph* g) { return g->s32; }
+template <class A> inline const A* scal_t(const hgl_graph* g);
+template <> inline const double* scal_t<double>(const hgl_graph* g) { return g->t; }
+template <> inline const float* scal_t<float>(const hgl_graph* g) { return g->t32; }
 }  // namespace hgl
 
 inline int hgl::tuned_chunk_vecs(const hgl_graph* g, int kind, int c) {

@@ -325,6 +325,27 @@ k_pc_expand_f32(const int32_t* __restrict__ exp_block, const int32_t* __restrict
   const int c0 = blockIdx.y * PF_C;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;  // tx: columns, ty: rows
   const int kk = (k + 3) & ~3;
+  // the accumulators start at R / (1+lam): these loads are issued first so that their
+  // latency overlaps the staging of the Q and C tiles
+  float acc[8][8];
+  const float* rbase = R + (base + ty * 4) * ldr + c0 + tx * 4;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int row = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+    const float* rrow = rbase + (int64_t)(i < 4 ? i : 60 + i) * ldr;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int col = c0 + h * 64 + tx * 4;
+      // ldr is a multiple of 4 and col of 4, so col < c keeps the whole vector inside
+      // the row; padding columns only reach accumulators that are never stored
+      float4 rv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + row < nrows && col < c) rv = __ldg(reinterpret_cast<const float4*>(rrow + h * 64));
+      acc[i][4 * h] = inv1l * rv.x;
+      acc[i][4 * h + 1] = inv1l * rv.y;
+      acc[i][4 * h + 2] = inv1l * rv.z;
+      acc[i][4 * h + 3] = inv1l * rv.w;
+    }
+  }
   for (int q = tid; q < PC_TILE * (PF_R / 4); q += 256) {
     const int i = q & (PC_TILE - 1), r = (q >> 7) * 4;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -341,11 +362,6 @@ k_pc_expand_f32(const int32_t* __restrict__ exp_block, const int32_t* __restrict
     *reinterpret_cast<float4*>(&cs[r * PF_C + j]) = v;
   }
   __syncthreads();
-  float acc[8][8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 #pragma unroll 4
   for (int r = 0; r < kk; ++r) {
     const float4 a0 = *reinterpret_cast<const float4*>(&qt[r * PC_TILE + ty * 4]);
@@ -358,20 +374,17 @@ k_pc_expand_f32(const int32_t* __restrict__ exp_block, const int32_t* __restrict
   for (int i = 0; i < 8; ++i) {
     const int row = i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4);
     if (i0 + row >= nrows) continue;
-    const float* rrow = R + (base + row) * ldr;
     float* zrow = Z + (base + row) * ldz;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int col = c0 + h * 64 + tx * 4;
       if (col + 3 < c) {
-        const float4 rv = __ldg(reinterpret_cast<const float4*>(rrow + col));
         *reinterpret_cast<float4*>(zrow + col) =
-            make_float4(fmaf(inv1l, rv.x, acc[i][4 * h]), fmaf(inv1l, rv.y, acc[i][4 * h + 1]),
-                        fmaf(inv1l, rv.z, acc[i][4 * h + 2]), fmaf(inv1l, rv.w, acc[i][4 * h + 3]));
+            make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
       } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          if (col + j < c) zrow[col + j] = fmaf(inv1l, rrow[col + j], acc[i][4 * h + j]);
+          if (col + j < c) zrow[col + j] = acc[i][4 * h + j];
       }
     }
   }

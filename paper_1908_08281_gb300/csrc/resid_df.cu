@@ -46,15 +46,24 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
   float* Th = static_cast<float*>(buffer_get(g->scratch, sizeof(float) * 2 * (size_t)g->m * cc, &stt));
   if (!Th) return stt;
   float* Tl = Th + (size_t)g->m * cc;
-  const int64_t cap = (int64_t)g->num_sms * 8;
-  const int grid1 = (int)(g->nheavy + std::max<int64_t>(1, std::min<int64_t>((g->m - g->nheavy + 7) / 8, cap)));
-  const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, cap));
+  // grids capped at the blocks resident at once (one wave; warps stride over rows)
+  auto grid_edge = [&](const void* fn) {
+    const int64_t cap = (int64_t)g->num_sms * std::min(8, resident_blocks(fn, df::THREADS, 0));
+    return (int)(g->nheavy + std::max<int64_t>(1, std::min<int64_t>((g->m - g->nheavy + 7) / 8, cap)));
+  };
+  auto grid_vertex = [&](const void* fn) {
+    const int64_t cap = (int64_t)g->num_sms * std::min(8, resident_blocks(fn, df::THREADS, 0));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 7) / 8, cap));
+  };
+  int grid2 = 1;
   ProfScope prof(HGL_PROF_RESIDUAL, st);
   for (int c0 = 0; c0 < c; c0 += cc) {
     const int cw = std::min(cc, c - c0);
 #define HGL_DF_CASE(LG_, NV_)                                                                                     \
   else if (lg == LG_ && nv == NV_) {                                                                              \
     count_launch(2);                                                                                              \
+    const int grid1 = grid_edge(reinterpret_cast<const void*>(df::k_edge<LG_, NV_>));                              \
+    grid2 = grid_vertex(reinterpret_cast<const void*>(df::k_vertex<LG_, NV_>));                                    \
     df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy,   \
                                                         s_hi, s_lo, t_hi, t_lo, Fh, Fl, ld32, c0, cw, Th, Tl,    \
                                                         (int64_t)cc);                                            \

@@ -29,8 +29,8 @@ constexpr int OP_WARPS = OP_THREADS / 32;
 template <class TX, class TT, int LG, int NV>
 __device__ __forceinline__ void edge_heavy_block(const int64_t* __restrict__ csc_ptr,
                                                  const int32_t* __restrict__ csc_idx,
-                                                 const int32_t* __restrict__ order, const double* __restrict__ s,
-                                                 const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx,
+                                                 const int32_t* __restrict__ order, const typename AccOf<TX>::type* __restrict__ s,
+                                                 const typename AccOf<TX>::type* __restrict__ t, const TX* __restrict__ X, int64_t ldx,
                                                  int c0, int cw, TT* __restrict__ Tp, int64_t ldt) {
   using A = typename AccOf<TX>::type;
   constexpr int E = 16 / (int)sizeof(TX);
@@ -94,8 +94,8 @@ __device__ __forceinline__ void edge_heavy_block(const int64_t* __restrict__ csc
 template <class TX, class TT, int LG, int NV>
 __global__ void __launch_bounds__(OP_THREADS)
 k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-            const int32_t* __restrict__ order, int64_t nheavy, const double* __restrict__ s,
-            const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx, int c0, int cw, TT* __restrict__ Tp,
+            const int32_t* __restrict__ order, int64_t nheavy, const typename AccOf<TX>::type* __restrict__ s,
+            const typename AccOf<TX>::type* __restrict__ t, const TX* __restrict__ X, int64_t ldx, int c0, int cw, TT* __restrict__ Tp,
             int64_t ldt, const int32_t* __restrict__ run_flag) {
   if (run_flag && *run_flag == 0) return;
   using A = typename AccOf<TX>::type;
@@ -178,7 +178,7 @@ k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
 template <class TX, class TT, class TZ, int LG, int NV, int EPI>
 __global__ void __launch_bounds__(OP_THREADS)
 k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
-              const double* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
+              const typename AccOf<TX>::type* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
               int64_t ldx, TZ* __restrict__ Z, int64_t ldz, int c0, int cw, int c, double a, double b,
               const double* __restrict__ Y, int64_t ldy, double gy, double* __restrict__ partials,
               const int32_t* __restrict__ run_flag) {
@@ -301,8 +301,8 @@ constexpr int RU = 4;
 template <class TX, class TT, int LG>
 __global__ void __launch_bounds__(OP_THREADS)
 k_edge_rows(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-            const int32_t* __restrict__ order, int64_t nheavy, const double* __restrict__ s,
-            const double* __restrict__ t, const TX* __restrict__ X, int64_t ldx, int c0, int cw, TT* __restrict__ Tp,
+            const int32_t* __restrict__ order, int64_t nheavy, const typename AccOf<TX>::type* __restrict__ s,
+            const typename AccOf<TX>::type* __restrict__ t, const TX* __restrict__ X, int64_t ldx, int c0, int cw, TT* __restrict__ Tp,
             int64_t ldt, const int32_t* __restrict__ run_flag) {
   if (run_flag && *run_flag == 0) return;
   using A = typename AccOf<TX>::type;
@@ -364,7 +364,7 @@ k_edge_rows(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
 template <class TX, class TT, class TZ, int LG, int EPI>
 __global__ void __launch_bounds__(OP_THREADS)
 k_vertex_rows(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
-              const double* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
+              const typename AccOf<TX>::type* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
               int64_t ldx, TZ* __restrict__ Z, int64_t ldz, int c0, int cw, int c, double a, double b,
               const double* __restrict__ Y, int64_t ldy, double gy, double* __restrict__ partials,
               const int32_t* __restrict__ run_flag) {

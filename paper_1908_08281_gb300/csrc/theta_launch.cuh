@@ -9,17 +9,20 @@ namespace hgl {
 inline int default_chunk_vecs() { return 32; }
 
 // Blocks of the hyperedge pass: one per heavy hyperedge, then enough for the light
-// rows (capped at 8 resident blocks per SM; warps stride over the remaining rows).
-inline int edge_grid(const hgl_graph* g) {
+// rows, capped at the blocks that are resident at once (per_sm per SM, at most 8) so
+// that the light part runs in a single wave; warps stride over the remaining rows.
+inline int edge_grid(const hgl_graph* g, int per_sm = 8) {
   const int64_t light = g->m - g->nheavy;
   int64_t need = (light + OP_WARPS - 1) / OP_WARPS;
-  int64_t cap = (int64_t)g->num_sms * 8;
+  int64_t cap = (int64_t)g->num_sms * (per_sm < 8 ? per_sm : 8);
   return (int)(g->nheavy + (need < cap ? (need > 0 ? need : 1) : cap));
 }
 
-inline int vertex_grid(const hgl_graph* g) {
+// Blocks of the vertex pass (also the row count of its reduction partials); the
+// default is the largest grid any instantiation uses.
+inline int vertex_grid(const hgl_graph* g, int per_sm = 8) {
   int64_t need = (g->n + OP_WARPS - 1) / OP_WARPS;
-  int64_t cap = (int64_t)g->num_sms * 8;
+  int64_t cap = (int64_t)g->num_sms * (per_sm < 8 ? per_sm : 8);
   return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
@@ -51,28 +54,49 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   TT* Tp = cl.scratch ? static_cast<TT*>(cl.scratch)
                       : static_cast<TT*>(buffer_get(g->scratch, sizeof(TT) * (size_t)g->m * (size_t)cc, &stt));
   if (!Tp) return stt;
-  const int grid1 = edge_grid(g), grid2 = vertex_grid(g);
+  int grid2 = vertex_grid(g);
+  using A = typename AccOf<TX>::type;
+  const A* sA = scal_s<A>(g);
+  const A* tA = scal_t<A>(g);
   ProfScope prof(HGL_PROF_OPERATOR, st);
   const TX* X = static_cast<const TX*>(cl.X);
   TZ* Z = static_cast<TZ*>(cl.Z);
   for (int c0 = 0; c0 < cl.c; c0 += cc) {
     const int cw = cl.c - c0 < cc ? cl.c - c0 : cc;
-#define HGL_EDGE_CASE(LG_, NV_)                                                                       \
-  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_edge_pass<TX, TT, LG_, NV_><<<grid1, OP_THREADS, 0, st>>>(          \
-      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc,   \
-      cl.run_flag);
-#define HGL_VERTEX_CASE(LG_, NV_)                                                                     \
-  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
-      g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
-      cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
-#define HGL_EDGE_ROWS(LG_)                                                                            \
-  else if (lg == LG_) hgl::count_launch(), k_edge_rows<TX, TT, LG_><<<grid1, OP_THREADS, 0, st>>>(         \
-      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, X, cl.ldx, c0, cw, Tp, (int64_t)cc,   \
-      cl.run_flag);
-#define HGL_VERTEX_ROWS(LG_)                                                                          \
-  else if (lg == LG_) hgl::count_launch(), k_vertex_rows<TX, TT, TZ, LG_, EPI><<<grid2, OP_THREADS, 0, st>>>( \
-      g->n, g->csr_ptr, g->csr_idx, g->s, Tp, (int64_t)cc, X, cl.ldx, Z, cl.ldz, c0, cw, cl.c, cl.a, cl.b,  \
-      cl.Y, cl.ldy, cl.gy, cl.partials, cl.run_flag);
+#define HGL_EDGE_CASE(LG_, NV_)                                                                        \
+  else if (lg == LG_ && nv == NV_) {                                                                   \
+    auto fn = k_edge_pass<TX, TT, LG_, NV_>;                                                           \
+    const int gr = edge_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));    \
+    hgl::count_launch();                                                                               \
+    fn<<<gr, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, sA, tA, X,   \
+                                  cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);                       \
+  }
+#define HGL_VERTEX_CASE(LG_, NV_)                                                                      \
+  else if (lg == LG_ && nv == NV_) {                                                                   \
+    auto fn = k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI>;                                                \
+    grid2 = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));         \
+    hgl::count_launch();                                                                               \
+    fn<<<grid2, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, sA, Tp, (int64_t)cc, X, cl.ldx, Z,  \
+                                     cl.ldz, c0, cw, cl.c, cl.a, cl.b, cl.Y, cl.ldy, cl.gy, cl.partials, \
+                                     cl.run_flag);                                                     \
+  }
+#define HGL_EDGE_ROWS(LG_)                                                                             \
+  else if (lg == LG_) {                                                                                \
+    auto fn = k_edge_rows<TX, TT, LG_>;                                                                \
+    const int gr = edge_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));    \
+    hgl::count_launch();                                                                               \
+    fn<<<gr, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, sA, tA, X,   \
+                                  cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);                       \
+  }
+#define HGL_VERTEX_ROWS(LG_)                                                                           \
+  else if (lg == LG_) {                                                                                \
+    auto fn = k_vertex_rows<TX, TT, TZ, LG_, EPI>;                                                     \
+    grid2 = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));         \
+    hgl::count_launch();                                                                               \
+    fn<<<grid2, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, sA, Tp, (int64_t)cc, X, cl.ldx, Z,  \
+                                     cl.ldz, c0, cw, cl.c, cl.a, cl.b, cl.Y, cl.ldy, cl.gy, cl.partials, \
+                                     cl.run_flag);                                                     \
+  }
     if (nv == 1 && lg <= 8) {
       // narrow chunk: one row per group of lanes
       if (false) {

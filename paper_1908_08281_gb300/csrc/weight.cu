@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "solver.cuh"
-#include "theta_kernels.cuh"
+#include "theta_launch.cuh"
 
 namespace hgl {
 
@@ -25,7 +25,7 @@ namespace {
 template <class TX, int LG, int NV, bool DUAL>
 __global__ void __launch_bounds__(OP_THREADS)
 k_grad_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
-            const int32_t* __restrict__ order, int64_t nheavy, const double* __restrict__ s,
+            const int32_t* __restrict__ order, int64_t nheavy, const typename AccOf<TX>::type* __restrict__ s,
             const double* __restrict__ t, const TX* __restrict__ F, const TX* __restrict__ Zb, int64_t ld, int c0,
             int cw, typename AccOf<TX>::type* __restrict__ TF, typename AccOf<TX>::type* __restrict__ TZ, int64_t ldt,
             double* __restrict__ ex) {
@@ -244,18 +244,25 @@ hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld
   double* phi = vecs + g->m;
   const int64_t cap = (int64_t)g->num_sms * 8;
   const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + OP_WARPS - 1) / OP_WARPS, cap));
-  const int grid1h =
-      (int)(g->nheavy + std::max<int64_t>(1, std::min<int64_t>((g->m - g->nheavy + OP_WARPS - 1) / OP_WARPS, cap)));
-  const int grid2 = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + OP_WARPS - 1) / OP_WARPS, cap));
   ProfScope prof(HGL_PROF_GRADIENT, st);
   for (int c0 = 0; c0 < c; c0 += cc) {
     const int cw = std::min(cc, c - c0);
 #define HGL_GE(LG_, NV_)                                                                                        \
-  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_edge<TX, LG_, NV_, DUAL><<<grid1h, OP_THREADS, 0, st>>>(                \
-      g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, g->s, g->t, F, Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);
+  else if (lg == LG_ && nv == NV_) {                                                                            \
+    auto fn = k_grad_edge<TX, LG_, NV_, DUAL>;                                                                  \
+    const int gr = edge_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));             \
+    hgl::count_launch();                                                                                        \
+    fn<<<gr, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, scal_s<A>(g), g->t, F, \
+                                  Zb, ld, c0, cw, TF, TZ, (int64_t)cc, ex);                                     \
+  }
 #define HGL_GV(LG_, NV_)                                                                                        \
-  else if (lg == LG_ && nv == NV_) hgl::count_launch(), k_grad_vertex<TX, LG_, NV_, DUAL><<<grid2, OP_THREADS, 0, st>>>(               \
-      g->n, g->csr_ptr, g->csr_idx, g->s, TF, TZ, (int64_t)cc, F, Zb, ld, c0, cw, phi);
+  else if (lg == LG_ && nv == NV_) {                                                                            \
+    auto fn = k_grad_vertex<TX, LG_, NV_, DUAL>;                                                                \
+    const int gr = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));           \
+    hgl::count_launch();                                                                                        \
+    fn<<<gr, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, g->s, TF, TZ, (int64_t)cc, F, Zb, ld, c0, cw,    \
+                                  phi);                                                                         \
+  }
     if (false) {
     }
     HGL_FOR_EACH_TILE(HGL_GE)
