@@ -220,6 +220,63 @@ def weight_grad(H, w, F, mu: float, dv_frozen: bool = False) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# differentiation through the solve (adjoint method)
+# ----------------------------------------------------------------------------
+
+
+def adjoint_solve(H, w, lam: float, G, dense: bool = True, tol: float = 1e-13) -> np.ndarray:
+    """Z = M^-1 G.  M = (1+lam) I - Theta is symmetric, so the adjoint of the ranking
+    system (Eq. 6) has the same operator; the transposed right-hand side is G."""
+    G = np.asarray(G, dtype=np.float64)
+    if dense:
+        return np.linalg.solve(system_dense(H, w, lam), G)
+    return cg_solve(H, w, lam, G / lam, tol=tol)["F"]
+
+
+def solve_grad_w(H, w, lam: float, F, G, dv_frozen: bool = False, dense: bool = True):
+    """d/dw of <G, F(w)> where M(w) F = lam Y, at fixed G (the gradient of a loss with
+    respect to F).  Differentiating M F = lam Y gives dF = -M^-1 (dM) F, and
+    dM/dw_e = -dTheta/dw_e, so with Z = M^-1 G
+
+        <G, dF/dw_e> = d/dw_e tr(Z^T Theta(w) F)   (Z and F held fixed),
+
+    the bilinear gradient of Eq. 1.  Returns (gradient[m], Z)."""
+    Z = adjoint_solve(H, w, lam, G, dense=dense)
+    return bilinear_theta_grad(H, w, F, Z, dv_frozen), Z
+
+
+def zhou_loss(H, w, Y, lam: float, mu: float, F=None):
+    """L(w) = tr(F^T Delta F) + lam ||F - Y||^2 + mu ||w||^2 at F = F(w) (Eq. 4 with the
+    ranking term of Eq. 3).  Returns (L, F, dL/dF at fixed w, explicit dL/dw at fixed F)."""
+    if F is None:
+        F = solve_dense(H, w, lam, Y)
+    L = full_loss(H, w, F, Y, lam, mu)
+    dF = 2.0 * theta_apply(H, w, F, 1.0, -1.0) + 2.0 * lam * (F - np.asarray(Y, np.float64))
+    dw = weight_grad(H, w, F, mu)
+    return L, F, dF, dw
+
+
+def heldout_loss(H, w, Y, lam: float, rows, Y_test, F=None):
+    """L(w) = ||F(w)[rows] - Y_test||^2: a loss on held-out vertices with no explicit
+    dependence on w, whose adjoint right-hand side does not vanish at the solution.
+    Returns (L, F, dL/dF, explicit dL/dw = 0)."""
+    if F is None:
+        F = solve_dense(H, w, lam, Y)
+    D = F[rows] - np.asarray(Y_test, np.float64)
+    dF = np.zeros_like(F)
+    dF[rows] = 2.0 * D
+    return float((D * D).sum()), F, dF, np.zeros(np.asarray(w).shape[0])
+
+
+def total_grad(H, w, Y, lam: float, loss, dense: bool = True, **kw):
+    """dL/dw = explicit dL/dw + <dL/dF, dF/dw> (adjoint term), for ``loss`` one of
+    ``zhou_loss`` / ``heldout_loss`` (extra keyword arguments go to the loss)."""
+    L, F, dF, dw = loss(H, w, Y, lam, **kw)
+    adj, Z = solve_grad_w(H, w, lam, F, dF, dense=dense)
+    return L, dw + adj, adj, Z
+
+
+# ----------------------------------------------------------------------------
 # simplex projection (Eq. 5 read as a Euclidean projection)
 # ----------------------------------------------------------------------------
 
