@@ -332,6 +332,35 @@ hgl_status hgl_weight_grad(const hgl_graph* g, const double* w, const void* F,
 hgl_status hgl_project_simplex(double* w, const double* grad, double eta, int64_t m,
                                void* stream);
 
+/*
+ * hgl_adjoint_grad -- the part of dL/dw that flows through the ranking solve, for a
+ * loss L(F(w), w) with F(w) the solution of M(w) F = lam Y (Eq. 6), by the adjoint
+ * method.  Differentiating M F = lam Y gives dF = -M^-1 (dM) F with dM/dw_e =
+ * -dTheta/dw_e (Eq. 1, dv(w) included), so for G = dL/dF
+ *     grad_e = <G, dF/dw_e> = d/dw_e tr(Z^T Theta(w) F),   Z = M^-1 G,
+ * computed by one batched CG solve of M Z = G (M is symmetric, so the "transposed"
+ * system has the same operator) followed by the bilinear form of the Eq. 4 gradient.
+ * The explicit dependence of L on w (e.g. the mu ||w||^2 term or the Delta in
+ * tr(F^T Delta F), see hgl_weight_grad) is not included: add it.  The paper has no
+ * counterpart; the forward solve's iterates are not needed (only F).
+ *   w          device FP64[m];  lam > 0 (the lam of the forward solve)
+ *   F          device FP64 panel n x c: the forward solution
+ *   G          device FP64 panel n x c: dL/dF
+ *   Z          device FP64 panel n x c, out: M^-1 G (must not alias F or G)
+ *   ld         leading dimension shared by F, G and Z
+ *   precond    NULL or a preconditioner from hgl_block_rsvd for (w, lam)
+ *   opts       solve options for the adjoint CG (tol relative to ||G_j||, dtype:
+ *              FP64 or a mixed mode, as in hgl_cg_solve)
+ *   grad       device FP64[m], out
+ *   stats      optional host out: statistics of the adjoint solve
+ * Returns the adjoint solve's status (HGL_ERR_NOT_CONVERGED still writes Z and grad).
+ * Synchronises `stream`.
+ */
+hgl_status hgl_adjoint_grad(hgl_graph* g, const double* w, double lam, const double* F,
+                            const double* G, double* Z, int64_t ld, int32_t c,
+                            const hgl_precond* precond, const hgl_solve_opts* opts,
+                            double* grad, hgl_solve_stats* stats, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Adaptive outer iteration (Section 2: F at fixed w, then w at fixed F)      */
 /* ------------------------------------------------------------------------- */

@@ -271,7 +271,7 @@ int cg_iteration_bound(double lam, double tol) {
   return (int)std::ceil(std::log(2.0 / tol) / std::log(rate)) + 2;
 }
 
-hgl_status true_residual(hgl_graph* g, const SolverMem& sm, double lam, const double* Y, int64_t ldy,
+hgl_status true_residual(hgl_graph* g, const SolverMem& sm, double lam, double gy, const double* Y, int64_t ldy,
                          const double* F, int64_t ldf, void* Rout, int rdt, int64_t ldr, cudaStream_t st) {
   OpCall cl{};
   cl.g = g;
@@ -287,7 +287,7 @@ hgl_status true_residual(hgl_graph* g, const SolverMem& sm, double lam, const do
   cl.epi = EPI_RESID;
   cl.Y = Y;
   cl.ldy = ldy;
-  cl.gy = lam;
+  cl.gy = gy;
   cl.partials = sm.pa;
   cl.chunk_cols = g->chunk_cols;
   int rows = 0;
@@ -333,7 +333,7 @@ hgl_status fill_stats(const SolverMem& sm, int total_iters, int refinements, dou
   return HGL_OK;
 }
 
-hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double* Y, int64_t ldy, double* F,
+hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, const double* Y, int64_t ldy, double* F,
                          int64_t ldf, int c, const hgl_precond* P, const hgl_solve_opts& o, double* relres_out,
                          int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready,
                          SolveExtras* extras) {
@@ -350,7 +350,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   if (P) HGL_TRY(precond_check(P, g, lam));
 
   int rows = 0;
-  HGL_TRY((panel_dot<double, double>(g, c, Y, ldy, Y, ldy, lam * lam, sm.pa, st, &rows)));
+  HGL_TRY((panel_dot<double, double>(g, c, Y, ldy, Y, ldy, gy * gy, sm.pa, st, &rows)));
   HGL_TRY(cg_reduce<RED_B2>(sm.pa, nullptr, rows, S, st));
   hgl::count_launch(); k_set_target<<<(c + 255) / 256, 256, 0, st>>>(S, tol * tol);
   HGL_CHECK_CUDA(cudaGetLastError());
@@ -360,9 +360,9 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
   if (mode == HGL_FP64) {
     double* R = static_cast<double*>(sm.R);
     if (warm) {
-      HGL_TRY(true_residual(g, sm, lam, Y, ldy, F, ldf, R, HGL_FP64, sm.ld64, st));
+      HGL_TRY(true_residual(g, sm, lam, gy, Y, ldy, F, ldf, R, HGL_FP64, sm.ld64, st));
     } else {
-      HGL_TRY((panel_scale<double, double, false>(g, c, Y, ldy, lam, R, sm.ld64, nullptr, st, nullptr)));
+      HGL_TRY((panel_scale<double, double, false>(g, c, Y, ldy, gy, R, sm.ld64, nullptr, st, nullptr)));
     }
     int rows_b = 0;
     const double* zsrc = R;
@@ -384,7 +384,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
     int done = 0;
     HGL_TRY((run_cg_loop<double, double>(g, sm, lam, F, ldf, HGL_FP64, HGL_FP64, P, max_iter,
                                          cg_iteration_bound(lam, tol), st, &done)));
-    HGL_TRY(true_residual(g, sm, lam, Y, ldy, F, ldf, sm.Q, HGL_FP64, sm.ld64, st));
+    HGL_TRY(true_residual(g, sm, lam, gy, Y, ldy, F, ldf, sm.Q, HGL_FP64, sm.ld64, st));
     HGL_TRY(fill_stats(sm, done, 0, tol, relres_out, iters_out, stats, st, &verdict));
     return verdict;
   }
@@ -405,7 +405,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double
     {
       int rr_rows = 0;
       HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0,
-                          lam, c, R32, sm.pa, st, &rr_rows));
+                          gy, c, R32, sm.pa, st, &rr_rows));
       HGL_TRY(cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, S, st));
     }
     HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
@@ -511,6 +511,6 @@ extern "C" hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double l
   if (opts) o = *opts;
   if (o.dtype != HGL_FP64 && o.dtype != HGL_FP32 && o.dtype != HGL_BF16)
     return hgl::record_error(HGL_ERR_INVALID_ARG, "unknown solve dtype");
-  return hgl::cg_solve_impl(const_cast<hgl_graph*>(g), w, lam, Y, ldy, F, ldf, c, precond, o, relres, iters, stats,
+  return hgl::cg_solve_impl(const_cast<hgl_graph*>(g), w, lam, lam, Y, ldy, F, ldf, c, precond, o, relres, iters, stats,
                             hgl::as_stream(stream), false, nullptr);
 }

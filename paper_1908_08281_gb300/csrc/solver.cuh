@@ -48,12 +48,20 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
 
 hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
 
-hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, const double* Y, int64_t ldy, double* F,
+// Solves M F = gy Y with M = (1 + lam) I - Theta (gy = lam for the ranking system of
+// Eq. 6, gy = 1 for the adjoint system M Z = G); relative residuals are taken against
+// ||gy y_j||.
+hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, const double* Y, int64_t ldy, double* F,
                          int64_t ldf, int c, const hgl_precond* P, const hgl_solve_opts& o, double* relres_out,
                          int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, bool degrees_ready,
                          SolveExtras* extras);
 
 int cg_iteration_bound(double lam, double tol);
+
+// grad = -theta_sign * d tr(Zb^T Theta F)/dw + 2 mu w (Zb = NULL: Zb = F), at fixed panels.
+hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
+                              int dtype, double mu, int flags, double* grad, cudaStream_t st,
+                              double theta_sign = 1.0);
 
 // per-column partial sums of A.B for panels of type dt (FP64 or FP32); rows in *rows
 hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,

@@ -9,8 +9,6 @@
 
 namespace hgl {
 
-hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
-                              int dtype, double mu, int flags, double* grad, cudaStream_t st);
 hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
                           cudaStream_t st, int max_steps);
 size_t project_work_doubles(int64_t m, int sms);
@@ -77,7 +75,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
   so.flags |= HGL_SOLVE_WARM_START;
   hgl_solve_stats ss{};
   SolveExtras ext;
-  hgl_status solve_status = cg_solve_impl(g, w, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true,
+  hgl_status solve_status = cg_solve_impl(g, w, o.lam, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true,
                                           &ext);
   if (P) hgl_precond_destroy(P);
   if (solve_status != HGL_OK && solve_status != HGL_ERR_NOT_CONVERGED) return solve_status;

@@ -206,7 +206,7 @@ k_grad_vertex(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
 __global__ void k_grad_final(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
                              const int32_t* __restrict__ de, const double* __restrict__ ex,
                              const double* __restrict__ phi, const double* __restrict__ w, double mu,
-                             double* __restrict__ grad) {
+                             double theta_sign, double* __restrict__ grad) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -216,13 +216,13 @@ __global__ void k_grad_final(int64_t m, const int64_t* __restrict__ csc_ptr, con
       for (int64_t i = csc_ptr[e] + lane, end = csc_ptr[e + 1]; i < end; i += 32) acc += phi[csc_idx[i]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) grad[e] = -(ex[e] / (double)de[e] - acc) + 2.0 * mu * w[e];
+    if (lane == 0) grad[e] = -theta_sign * (ex[e] / (double)de[e] - acc) + 2.0 * mu * w[e];
   }
 }
 
 template <class TX, bool DUAL>
 hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld, int c, double mu, bool frozen,
-                             const double* w, double* grad, cudaStream_t st) {
+                             const double* w, double* grad, cudaStream_t st, double theta_sign) {
   using A = typename AccOf<TX>::type;
   constexpr int E = 16 / (int)sizeof(TX);
   const int nvec = (c + E - 1) / E;
@@ -276,7 +276,7 @@ hgl_status grad_launch_typed(hgl_graph* g, const TX* F, const TX* Zb, int64_t ld
     HGL_CHECK_CUDA(cudaGetLastError());
   }
   hgl::count_launch(); k_grad_final<<<grid1, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->de, ex, frozen ? nullptr : phi, w, mu,
-                                             grad);
+                                             theta_sign, grad);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -389,17 +389,18 @@ __global__ void k_proj_apply(const double* __restrict__ v, int64_t m, const Proj
 }  // namespace
 
 hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
-                              int dtype, double mu, int flags, double* grad, cudaStream_t st) {
+                              int dtype, double mu, int flags, double* grad, cudaStream_t st, double theta_sign) {
   const bool frozen = (flags & HGL_GRAD_DV_FROZEN) != 0;
+  const double sg = theta_sign;
   if (dtype == HGL_FP64) {
     if (Zb)
-      return grad_launch_typed<double, true>(g, (const double*)F, (const double*)Zb, ld, c, mu, frozen, w, grad, st);
-    return grad_launch_typed<double, false>(g, (const double*)F, nullptr, ld, c, mu, frozen, w, grad, st);
+      return grad_launch_typed<double, true>(g, (const double*)F, (const double*)Zb, ld, c, mu, frozen, w, grad, st, sg);
+    return grad_launch_typed<double, false>(g, (const double*)F, nullptr, ld, c, mu, frozen, w, grad, st, sg);
   }
   if (dtype == HGL_FP32) {
     if (Zb)
-      return grad_launch_typed<float, true>(g, (const float*)F, (const float*)Zb, ld, c, mu, frozen, w, grad, st);
-    return grad_launch_typed<float, false>(g, (const float*)F, nullptr, ld, c, mu, frozen, w, grad, st);
+      return grad_launch_typed<float, true>(g, (const float*)F, (const float*)Zb, ld, c, mu, frozen, w, grad, st, sg);
+    return grad_launch_typed<float, false>(g, (const float*)F, nullptr, ld, c, mu, frozen, w, grad, st, sg);
   }
   return record_error(HGL_ERR_INVALID_ARG, "gradient panels must be FP64 or FP32");
 }

@@ -88,6 +88,8 @@ _SIGNATURES = {
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
+    "hgl_adjoint_grad": (_I32, [_P, _P, _D, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P,
+                                ctypes.POINTER(SolveStats), _P]),
     "hgl_adaptive_step": (_I32, [_P, _P, ctypes.POINTER(StepOpts), _P, _I64, _P, _I64, _I32,
                                  ctypes.POINTER(StepStats), _P]),
 }
@@ -378,6 +380,31 @@ def weight_grad(g: Graph, w: torch.Tensor, F: torch.Tensor, mu: float = 0.0, Z: 
                                  HGL_GRAD_DV_FROZEN if dv_frozen else 0, ctypes.c_void_p(grad.data_ptr()),
                                  _stream(stream)))
     return grad
+
+
+def adjoint_grad(g: Graph, w: torch.Tensor, lam: float, F: torch.Tensor, G: torch.Tensor,
+                 Z: torch.Tensor | None = None, tol: float = 1e-10, max_iter: int = 1000, dtype: int = HGL_FP64,
+                 inner_tol: float = 0.0, max_refine: int = 0, precond: Precond | None = None, stream=None,
+                 raise_on_fail: bool = True):
+    """<G, dF/dw> for F = M(w)^-1 lam Y by the adjoint method: solves M Z = G and returns
+    (grad[m], Z, stats) with grad_e = d/dw_e tr(Z^T Theta F)."""
+    n, c = F.shape
+    pf, ld, dtf = _panel(F, "F")
+    pg, ldg, dtg = _panel(G, "G")
+    if Z is None:
+        Z = padded_panel(n, c, torch.float64, F.device)
+    pz, ldz, dtz = _panel(Z, "Z")
+    if dtf != HGL_FP64 or dtg != HGL_FP64 or dtz != HGL_FP64 or not (ld == ldg == ldz):
+        raise ValueError("F, G and Z must be float64 panels with one leading dimension")
+    grad = torch.empty(g.m, dtype=torch.float64, device=F.device)
+    opts = SolveOpts(tol, max_iter, dtype, inner_tol, max_refine, 0)
+    stats = SolveStats()
+    st = lib().hgl_adjoint_grad(g.handle, _vec(w, "w"), lam, pf, pg, pz, ld, c,
+                                precond.handle if precond is not None else None, ctypes.byref(opts),
+                                ctypes.c_void_p(grad.data_ptr()), ctypes.byref(stats), _stream(stream))
+    if st != 0 and (raise_on_fail or st not in (-7,)):
+        _check(st)
+    return grad, Z, stats
 
 
 def project_simplex(w: torch.Tensor, grad: torch.Tensor | None, eta: float, stream=None) -> torch.Tensor:
