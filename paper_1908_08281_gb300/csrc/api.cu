@@ -16,6 +16,7 @@ static thread_local char g_last_error[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 namespace {
 struct ProfRecord {
@@ -57,10 +58,22 @@ void prof_drain() {
 
 bool profiling() { return g_prof_on.load(std::memory_order_relaxed); }
 
+static thread_local std::vector<ProfEvent>* t_capture_sink = nullptr;
+
+void prof_capture_begin(std::vector<ProfEvent>* sink) { t_capture_sink = sink; }
+void prof_capture_end() { t_capture_sink = nullptr; }
+bool prof_capturing() { return t_capture_sink != nullptr; }
+
+// tokens >= 0 index the pending records; tokens <= -2 index the capture sink
 int prof_begin(int family, cudaStream_t st) {
   std::lock_guard<std::mutex> lock(g_prof_mutex);
   ProfRecord r{family, pool_get(), pool_get()};
   if (!r.start || !r.stop) return -1;
+  if (t_capture_sink) {
+    if (cudaEventRecordWithFlags(r.start, st, cudaEventRecordExternal) != cudaSuccess) return -1;
+    t_capture_sink->push_back(ProfEvent{family, r.start, r.stop});
+    return -2 - ((int)t_capture_sink->size() - 1);
+  }
   if (cudaEventRecord(r.start, st) != cudaSuccess) return -1;
   g_prof_records.push_back(r);
   return (int)g_prof_records.size() - 1;
@@ -68,7 +81,36 @@ int prof_begin(int family, cudaStream_t st) {
 
 void prof_end(int token, cudaStream_t st) {
   std::lock_guard<std::mutex> lock(g_prof_mutex);
+  if (token <= -2) {
+    const int i = -2 - token;
+    if (t_capture_sink && i < (int)t_capture_sink->size())
+      cudaEventRecordWithFlags((*t_capture_sink)[i].stop, st, cudaEventRecordExternal);
+    return;
+  }
   if (token >= 0 && token < (int)g_prof_records.size()) cudaEventRecord(g_prof_records[token].stop, st);
+}
+
+void prof_graph_add(const std::vector<ProfEvent>& recs) {
+  if (!profiling()) return;
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  for (const auto& r : recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+      g_prof_ms[r.family] += ms;
+      g_prof_count[r.family] += 1;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
+}
+
+void prof_graph_release(std::vector<ProfEvent>& recs) {
+  std::lock_guard<std::mutex> lock(g_prof_mutex);
+  for (const auto& r : recs) {
+    g_prof_pool.push_back(r.start);
+    g_prof_pool.push_back(r.stop);
+  }
+  recs.clear();
 }
 
 hgl_status record_error(hgl_status s, const char* fmt, ...) {
@@ -223,6 +265,7 @@ hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches)
 }
 
 void hgl_graph_destroy(hgl_graph* g) {
+  if (g) hgl::step_graph_destroy(g->step_graph);
   if (!g) return;
   cudaFree(g->csc_ptr);
   cudaFree(g->csc_idx);

@@ -93,6 +93,8 @@ __global__ void k_set_target(CgState S, double tol2) {
 // 0.1 tol / relres): ten times below what the outer tolerance still needs, so that
 // the FP32 rounding of the correction rarely forces another sweep (a sweep costs a
 // pair-arithmetic residual and a CG restart; the margin costs about one iteration).
+// Also sets *S.need = 1 when some column needs the sweep (captured solves zero it
+// before this kernel and guard the sweep's expensive launches with it).
 __global__ void k_inner_targets(CgState S, double tol, double inner_tol) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.c; j += gridDim.x * blockDim.x) {
     const double rel = S.relres[j];
@@ -101,6 +103,7 @@ __global__ void k_inner_targets(CgState S, double tol, double inner_tol) {
     } else {
       double want = fmax(inner_tol, 0.1 * tol / rel);
       S.target[j] = want * want * S.rr[j];
+      *S.need = 1;
     }
   }
 }
@@ -170,6 +173,7 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
   S.bad = iv + 2 * c;
   S.run_flag = iv + 3 * c;
   S.done = reinterpret_cast<unsigned*>(iv + 3 * c + 4);
+  S.need = iv + 3 * c + 8;
   sm->int_bytes = sizeof(int32_t) * 4 * (size_t)c + 64;
   sm->int_base = iv;
   // partials: two arrays of max(rows) x c
@@ -295,20 +299,18 @@ hgl_status true_residual(hgl_graph* g, const SolverMem& sm, double lam, double g
   return cg_reduce<RED_RESID>(sm.pa, nullptr, rows, sm.S, st);
 }
 
-hgl_status fill_stats(const SolverMem& sm, int total_iters, int refinements, double tol, double* relres_out,
+hgl_status fill_stats(const CgState& S, int c, int refinements, double tol, double* relres_out,
                       int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, hgl_status* verdict) {
-  const int c = sm.c;
   if (relres_out)
-    HGL_CHECK_CUDA(cudaMemcpyAsync(relres_out, sm.S.relres, sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
+    HGL_CHECK_CUDA(cudaMemcpyAsync(relres_out, S.relres, sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
   if (iters_out)
-    HGL_CHECK_CUDA(cudaMemcpyAsync(iters_out, sm.S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, st));
+    HGL_CHECK_CUDA(cudaMemcpyAsync(iters_out, S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToDevice, st));
   std::vector<double> rel(c);
   std::vector<int32_t> bad(c), its(c);
-  HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), sm.S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
-  HGL_CHECK_CUDA(cudaMemcpyAsync(bad.data(), sm.S.bad, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
-  HGL_CHECK_CUDA(cudaMemcpyAsync(its.data(), sm.S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(bad.data(), S.bad, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(its.data(), S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
-  (void)total_iters;
   int max_it = 0;
   for (int j = 0; j < c; ++j) max_it = std::max(max_it, (int)its[j]);
   int conv = 0, nbad = 0;
@@ -382,10 +384,18 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
     }
     HGL_TRY(cg_reduce<RED_INIT>(sm.pa, P ? sm.pb : nullptr, rows, S, st));
     int done = 0;
-    HGL_TRY((run_cg_loop<double, double>(g, sm, lam, F, ldf, HGL_FP64, HGL_FP64, P, max_iter,
-                                         cg_iteration_bound(lam, tol), st, &done)));
+    if (extras && extras->fixed_iters > 0) {
+      // capture mode: a fixed number of iterations, converged columns exit on the device
+      for (int k = 0; k < extras->fixed_iters; ++k)
+        HGL_TRY((cg_iteration<double, double>(g, sm, lam, F, ldf, HGL_FP64, HGL_FP64, P, st)));
+    } else {
+      HGL_TRY((run_cg_loop<double, double>(g, sm, lam, F, ldf, HGL_FP64, HGL_FP64, P, max_iter,
+                                           cg_iteration_bound(lam, tol), st, &done)));
+    }
     HGL_TRY(true_residual(g, sm, lam, gy, Y, ldy, F, ldf, sm.Q, HGL_FP64, sm.ld64, st));
-    HGL_TRY(fill_stats(sm, done, 0, tol, relres_out, iters_out, stats, st, &verdict));
+    if (extras) extras->state = S;
+    if (extras && extras->fixed_iters > 0) return HGL_OK;
+    HGL_TRY(fill_stats(S, c, 0, tol, relres_out, iters_out, stats, st, &verdict));
     return verdict;
   }
 
@@ -398,30 +408,31 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
   // formed from the pair in pair arithmetic (FP64-accurate, no FP64 arithmetic)
   HGL_TRY(df_split_scalings(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, st));
   HGL_TRY(df_panel_op(g, 0, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
-  int total = 0, sweeps = 0;
-  std::vector<double> rel(c), b2(c);
-  std::vector<int32_t> iters_acc(c, 0);
-  for (;;) {
-    {
-      int rr_rows = 0;
-      HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0,
-                          gy, c, R32, sm.pa, st, &rr_rows));
-      HGL_TRY(cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, S, st));
-    }
-    HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
-    HGL_CHECK_CUDA(cudaMemcpyAsync(b2.data(), S.b2, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
-    HGL_CHECK_CUDA(cudaStreamSynchronize(st));
-    bool all = true;
-    for (int j = 0; j < c; ++j)
-      if (b2[j] > 0 && !(rel[j] <= tol)) all = false;
-    if (all || sweeps >= max_refine || total >= max_iter) break;
-    hgl::count_launch(); k_inner_targets<<<(c + 255) / 256, 256, 0, st>>>(S, tol, inner_tol);
+  // FP64-accurate residual from the pair; with a guard, skipped (launches and
+  // reduction) when *guard == 0, leaving the previous relres in place
+  auto residual = [&](const int32_t* guard) -> hgl_status {
+    int rr_rows = 0;
+    HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0, gy,
+                        c, R32, sm.pa, st, &rr_rows, guard));
+    CgState Sg = S;
+    Sg.guard = guard;
+    return cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, Sg, st);
+  };
+  // one refinement sweep: inner targets, z0 = P^-1 r, CG on M d = r in FP32 (host-checked
+  // batches, or `fixed` iterations with device-side early exit), F += d in the pair.
+  // Guarded sweeps (captured solves) skip their expensive launches when no column
+  // needs them (S.need, set by k_inner_targets).
+  auto sweep = [&](double floor, int fixed, int budget, int* done, bool guarded) -> hgl_status {
+    const int32_t* guard = guarded ? S.need : nullptr;
+    if (guarded) HGL_CHECK_CUDA(cudaMemsetAsync(S.need, 0, sizeof(int32_t), st));
+    hgl::count_launch();
+    k_inner_targets<<<(c + 255) / 256, 256, 0, st>>>(S, tol, floor);
     HGL_CHECK_CUDA(cudaGetLastError());
     HGL_CHECK_CUDA(cudaMemset2DAsync(X32, sizeof(float) * sm.ld32, 0, sizeof(float) * c, g->n, st));
     int rows_b = 0;
     const float* zsrc = R32;
     if (P) {
-      HGL_TRY(precond_apply_launch(P, g, R32, sm.ld32, sm.Z, sm.ld32, c, HGL_FP32, sm.pb, st, &rows_b, nullptr));
+      HGL_TRY(precond_apply_launch(P, g, R32, sm.ld32, sm.Z, sm.ld32, c, HGL_FP32, sm.pb, st, &rows_b, guard));
       zsrc = static_cast<const float*>(sm.Z);
     }
     if (mode == HGL_BF16) {
@@ -431,38 +442,84 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
       HGL_CHECK_CUDA(cudaMemcpy2DAsync(sm.P, sizeof(float) * sm.ld32, zsrc, sizeof(float) * sm.ld32,
                                        sizeof(float) * c, g->n, cudaMemcpyDeviceToDevice, st));
     }
-    HGL_TRY((panel_dot<float, float>(g, c, R32, sm.ld32, R32, sm.ld32, 1.0, sm.pa, st, &rows)));
-    if (P && rows_b != rows) {
-      const int mx = std::max(rows, rows_b);
-      if (rows < mx) HGL_CHECK_CUDA(cudaMemsetAsync(sm.pa + (size_t)rows * c, 0, sizeof(double) * (size_t)(mx - rows) * c, st));
-      if (rows_b < mx) HGL_CHECK_CUDA(cudaMemsetAsync(sm.pb + (size_t)rows_b * c, 0, sizeof(double) * (size_t)(mx - rows_b) * c, st));
-      rows = mx;
+    int drows = 0;
+    HGL_TRY((panel_dot<float, float>(g, c, R32, sm.ld32, R32, sm.ld32, 1.0, sm.pa, st, &drows)));
+    if (P && rows_b != drows) {
+      const int mx = std::max(drows, rows_b);
+      if (drows < mx)
+        HGL_CHECK_CUDA(cudaMemsetAsync(sm.pa + (size_t)drows * c, 0, sizeof(double) * (size_t)(mx - drows) * c, st));
+      if (rows_b < mx)
+        HGL_CHECK_CUDA(cudaMemsetAsync(sm.pb + (size_t)rows_b * c, 0, sizeof(double) * (size_t)(mx - rows_b) * c, st));
+      drows = mx;
     }
-    HGL_TRY(cg_reduce<RED_INIT>(sm.pa, P ? sm.pb : nullptr, rows, S, st));
-    int done = 0;
-    const int first = cg_iteration_bound(lam, inner_tol) + 1;
-    if (mode == HGL_BF16) {
-      HGL_TRY((run_cg_loop<bf16_t, float>(g, sm, lam, X32, sm.ld32, HGL_BF16, HGL_FP32, P, max_iter - total, first,
-                                          st, &done)));
+    HGL_TRY(cg_reduce<RED_INIT>(sm.pa, P ? sm.pb : nullptr, drows, S, st));
+    if (fixed > 0) {
+      for (int k = 0; k < fixed; ++k) {
+        if (mode == HGL_BF16)
+          HGL_TRY((cg_iteration<bf16_t, float>(g, sm, lam, X32, sm.ld32, HGL_BF16, HGL_FP32, P, st)));
+        else
+          HGL_TRY((cg_iteration<float, float>(g, sm, lam, X32, sm.ld32, HGL_FP32, HGL_FP32, P, st)));
+      }
+      *done = fixed;
     } else {
-      HGL_TRY((run_cg_loop<float, float>(g, sm, lam, X32, sm.ld32, HGL_FP32, HGL_FP32, P, max_iter - total, first,
-                                         st, &done)));
+      const int first = cg_iteration_bound(lam, floor) + 1;
+      if (mode == HGL_BF16) {
+        HGL_TRY((run_cg_loop<bf16_t, float>(g, sm, lam, X32, sm.ld32, HGL_BF16, HGL_FP32, P, budget, first, st,
+                                            done)));
+      } else {
+        HGL_TRY((run_cg_loop<float, float>(g, sm, lam, X32, sm.ld32, HGL_FP32, HGL_FP32, P, budget, first, st,
+                                           done)));
+      }
     }
-    total += done;
-    std::vector<int32_t> it(c);
-    HGL_CHECK_CUDA(cudaMemcpyAsync(it.data(), S.iters, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, st));
-    HGL_TRY(df_panel_op(g, 1, c, nullptr, 0, sm.Fh, sm.Fl, sm.ld32, X32, st));
+    return df_panel_op(g, 1, c, nullptr, 0, sm.Fh, sm.Fl, sm.ld32, X32, st, guard);
+  };
+
+  if (extras && extras->fixed_iters > 0) {
+    // capture mode: a fixed launch sequence without host reads -- the residual, then two
+    // guarded sweeps each followed by a guarded residual.  A sweep aims at
+    // max(floor, 0.1 tol / relres); one FP32 sweep reaches about 1e-7 times the starting
+    // relres, so the second runs (on the device's decision) only when the first fell
+    // short.  Statistics stay on the device.
+    if (mode == HGL_BF16) return record_error(HGL_ERR_INVALID_ARG, "captured solves take FP64 or FP32 panels");
+    const double floor = o.inner_tol > 0 ? o.inner_tol : 1e-7;
+    int done = 0;
+    HGL_TRY(residual(nullptr));
+    for (int sw = 0; sw < 2; ++sw) {
+      HGL_TRY(sweep(floor, extras->fixed_iters, 0, &done, true));
+      HGL_TRY(residual(S.need));
+    }
+    HGL_TRY(df_panel_op(g, 2, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
+    extras->f32 = sm.Fh;
+    extras->ld32 = sm.ld32;
+    extras->state = S;
+    return HGL_OK;
+  }
+
+  // eager: sweep until every column meets tol (host-checked), iterations counted on
+  // the device across sweeps
+  int total = 0, sweeps = 0;
+  std::vector<double> rel(c), b2(c);
+  for (;;) {
+    HGL_TRY(residual(nullptr));
+    HGL_CHECK_CUDA(cudaMemcpyAsync(rel.data(), S.relres, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
+    HGL_CHECK_CUDA(cudaMemcpyAsync(b2.data(), S.b2, sizeof(double) * c, cudaMemcpyDeviceToHost, st));
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < c; ++j) iters_acc[j] += it[j];
+    bool all = true;
+    for (int j = 0; j < c; ++j)
+      if (b2[j] > 0 && !(rel[j] <= tol)) all = false;
+    if (all || sweeps >= max_refine || total >= max_iter) break;
+    int done = 0;
+    HGL_TRY(sweep(inner_tol, 0, max_iter - total, &done, false));
+    total += done;
     ++sweeps;
   }
   if (sweeps > 0) HGL_TRY(df_panel_op(g, 2, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
   if (extras) {
     extras->f32 = sm.Fh;
     extras->ld32 = sm.ld32;
+    extras->state = S;
   }
-  HGL_CHECK_CUDA(cudaMemcpyAsync(S.iters, iters_acc.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, st));
-  HGL_TRY(fill_stats(sm, total, sweeps > 0 ? sweeps - 1 : 0, tol, relres_out, iters_out, stats, st, &verdict));
+  HGL_TRY(fill_stats(S, c, sweeps > 0 ? sweeps - 1 : 0, tol, relres_out, iters_out, stats, st, &verdict));
   return verdict;
 }
 

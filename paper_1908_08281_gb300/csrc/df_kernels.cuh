@@ -74,7 +74,8 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
        const int32_t* __restrict__ order, int64_t nheavy, const float* __restrict__ s_hi,
        const float* __restrict__ s_lo, const float* __restrict__ t_hi, const float* __restrict__ t_lo,
        const float* __restrict__ Fh, const float* __restrict__ Fl, int64_t ldf, int c0, int cw,
-       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt) {
+       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt, const int32_t* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   constexpr int E = 4, G = 32 / LG, WARPS = THREADS / 32, TILE = LG * NV * E;
   const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
   f2 acc[NV][E];
@@ -165,7 +166,8 @@ k_vertex(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restri
          const float* __restrict__ s_hi, const float* __restrict__ s_lo, const float* __restrict__ Th,
          const float* __restrict__ Tl, int64_t ldt, const float* __restrict__ Fh, const float* __restrict__ Fl,
          int64_t ldf, const double* __restrict__ Y, int64_t ldy, double a, double b, double gy, int c0, int cw, int c,
-         float* __restrict__ R, int64_t ldr, double* __restrict__ partials) {
+         float* __restrict__ R, int64_t ldr, double* __restrict__ partials, const int32_t* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   constexpr int E = 4, G = 32 / LG, TILE = LG * NV * E;
   const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -257,7 +259,9 @@ enum PanelOp : int { SPLIT = 0, ACCUMULATE = 1, COMBINE = 2 };
 
 template <int OP>
 __global__ void k_panel(int64_t n, int c, double* __restrict__ F, int64_t ldf, float* __restrict__ Fh,
-                        float* __restrict__ Fl, int64_t ld32, const float* __restrict__ D) {
+                        float* __restrict__ Fl, int64_t ld32, const float* __restrict__ D,
+                        const int32_t* __restrict__ guard) {
+  if (guard && *guard == 0) return;
   const int vecs = (c + 3) / 4;
   const int64_t total = n * vecs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <map>
+#include <vector>
 #include <string>
 
 #include "../../include/hgl.h"
@@ -43,12 +44,27 @@ constexpr int64_t HEAVY_ROW = 128;
 
 // Process-wide count of kernels launched by the library (diagnostics).
 void count_launch(unsigned n = 1);
+void uncount_launch(unsigned long long n);  // launches recorded by a capture, not run
+struct StepGraph;
+void step_graph_destroy(StepGraph* sg);
 
 // Kernel timing: while profiling is enabled, ProfScope records an event pair on the
-// stream around the launches made in its lifetime.
+// stream around the launches made in its lifetime.  While a stream capture of this
+// thread has a sink installed, every ProfScope instead records its pair as event
+// nodes of the graph (cudaEventRecordExternal) into the sink, whose times are added
+// to the totals after each replay (prof_graph_add).
 bool profiling();
 int prof_begin(int family, cudaStream_t st);
 void prof_end(int token, cudaStream_t st);
+struct ProfEvent {
+  int family;
+  cudaEvent_t start, stop;
+};
+void prof_capture_begin(std::vector<ProfEvent>* sink);
+void prof_capture_end();
+bool prof_capturing();
+void prof_graph_add(const std::vector<ProfEvent>& recs);   // device synchronised by the caller
+void prof_graph_release(std::vector<ProfEvent>& recs);
 // Time the statements (launches) passed as the macro's trailing argument on stream `st`.
 #define HGL_PROFILED(FAM, ...)                 \
   do {                                         \
@@ -58,9 +74,10 @@ void prof_end(int token, cudaStream_t st);
 struct ProfScope {
   int token;
   cudaStream_t st;
-  ProfScope(int family, cudaStream_t s) : token(profiling() ? prof_begin(family, s) : -1), st(s) {}
+  ProfScope(int family, cudaStream_t s)
+      : token(profiling() || prof_capturing() ? prof_begin(family, s) : -1), st(s) {}
   ~ProfScope() {
-    if (token >= 0) prof_end(token, st);
+    if (token != -1) prof_end(token, st);
   }
 };
 
@@ -96,6 +113,8 @@ struct hgl_graph {
   // (panel kind, c); kind = HGL_FP64/FP32/BF16 for the operator, TUNE_PAIR for the
   // pair-arithmetic residual
   std::map<uint64_t, int> tuned_chunk;
+  // the captured CUDA graph of hgl_adaptive_step (HGL_STEP_GRAPH), if any
+  hgl::StepGraph* step_graph = nullptr;
 };
 
 #define HGL_CHECK_CUDA(call)                                                   \

@@ -483,6 +483,20 @@ hgl_status precond_check(const hgl_precond* P, const hgl_graph* g, double lam) {
   return HGL_OK;
 }
 
+hgl_status precond_reserve(hgl_precond* P, int c, int dt) {
+  hgl_status s = HGL_OK;
+  const bool f32q = P->dtype == HGL_BF16;
+  if (dt == HGL_FP32 && f32q && P->k <= PF_R && P->k % 4 == 0) {
+    const int64_t ldp = (c + 3) / 4 * 4;
+    if (!buffer_get(P->pbuf, sizeof(float) * (size_t)P->nslabs * PF_R * ldp, &s)) return s;
+    if (!buffer_get(P->cbuf, sizeof(float) * (size_t)P->nb * PF_R * ldp, &s)) return s;
+  } else {
+    const size_t a = dt == HGL_FP64 ? sizeof(double) : sizeof(float);
+    if (!buffer_get(P->cbuf, a * (size_t)P->nb * P->k * c, &s)) return s;
+  }
+  return HGL_OK;
+}
+
 hgl_status precond_apply_launch(const hgl_precond* Pc, const hgl_graph* g, const void* R, int64_t ldr, void* Z,
                                 int64_t ldz, int c, int dt, double* partials_rz, cudaStream_t st, int* rows,
                                 const int32_t* run_flag) {

@@ -19,15 +19,15 @@ hgl_status df_split_scalings(const hgl_graph* g, float* s_hi, float* s_lo, float
 }
 
 hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf, float* Fh, float* Fl, int64_t ld32,
-                       const float* D, cudaStream_t st) {
+                       const float* D, cudaStream_t st, const int32_t* guard) {
   const int blocks = g->num_sms * 8;
   count_launch();
   if (op == df::SPLIT)
-    df::k_panel<df::SPLIT><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+    df::k_panel<df::SPLIT><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D, guard);
   else if (op == df::ACCUMULATE)
-    df::k_panel<df::ACCUMULATE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+    df::k_panel<df::ACCUMULATE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D, guard);
   else
-    df::k_panel<df::COMBINE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D);
+    df::k_panel<df::COMBINE><<<blocks, 256, 0, st>>>(g->n, c, F, ldf, Fh, Fl, ld32, D, guard);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -35,7 +35,8 @@ hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf
 // R = fl32(gy Y + a F + b Theta F) with F = Fh + Fl; partials of R.R (rows returned).
 hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
                        const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
-                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows) {
+                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows,
+                       const int32_t* guard) {
   constexpr int E = 4;
   const int nvec = (c + E - 1) / E;
   int lg = 1, nv = 1;
@@ -66,10 +67,10 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
     grid2 = grid_vertex(reinterpret_cast<const void*>(df::k_vertex<LG_, NV_>));                                    \
     df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy,   \
                                                         s_hi, s_lo, t_hi, t_lo, Fh, Fl, ld32, c0, cw, Th, Tl,    \
-                                                        (int64_t)cc);                                            \
+                                                        (int64_t)cc, guard);                                     \
     df::k_vertex<LG_, NV_><<<grid2, df::THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, s_hi, s_lo, Th, Tl,     \
                                                           (int64_t)cc, Fh, Fl, ld32, Y, ldy, a, b, gy, c0, cw, c, \
-                                                          R, ld32, partials);                                     \
+                                                          R, ld32, partials, guard);                              \
   }
     if (false) {
     }

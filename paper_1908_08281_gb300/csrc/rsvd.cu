@@ -99,7 +99,7 @@ struct Work {
 
 inline size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 
-hgl_status plan(hgl_graph* g, const int64_t* bp, int nb, int k, int l, int lpad, int dtype, Work* w) {
+hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, int l, int lpad, int dtype, Work* w) {
   const bool bf16 = dtype == HGL_BF16;
   w->v0.resize(nb);
   w->arow.resize(nb);
@@ -149,7 +149,7 @@ hgl_status plan(hgl_graph* g, const int64_t* bp, int nb, int k, int l, int lpad,
   const size_t oEv = take(8 * (size_t)nb * lpad);
   const size_t oMeta = take(8 * 3 * (size_t)nb + 4 * 3 * (size_t)nb + 4 * 2 * nu + 64);
   hgl_status st = HGL_OK;
-  char* base = static_cast<char*>(buffer_get(g->rsvd, off, &st));
+  char* base = static_cast<char*>(buffer_get(space, off, &st));
   if (!base) return st;
   w->A = base + oA;
   w->St = base + oSt;
@@ -271,11 +271,20 @@ hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool writ
 
 }  // namespace
 
-hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const int64_t* bp, int32_t nb, int32_t k,
-                         int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st, hgl_precond** out,
-                         bool degrees_ready) {
-  hgl_graph* g = const_cast<hgl_graph*>(gc);
-  *out = nullptr;
+// A block rSVD plan: the host metadata and device work space of one block layout
+// (Work), and the preconditioner handle its builds write.  Creating it allocates and
+// uploads; computing it only launches kernels, so a plan can be rebuilt inside a
+// captured CUDA graph.
+struct PrecondPlan {
+  Work wk;
+  hgl_precond* P = nullptr;
+  Buffer own;            // the plan's own work space (graph plans); else g->rsvd
+  int dtype = HGL_BF16;
+  int q = 0;
+};
+
+hgl_status precond_validate(const hgl_graph* g, const int64_t* bp, int32_t nb, int32_t k, int32_t p, int32_t q,
+                            int gemm_dtype) {
   if (!bp || nb < 1) return record_error(HGL_ERR_INVALID_ARG, "block_ptr is NULL or nblocks < 1");
   if (k < 1 || p < 0 || q < 0 || k + p > MAX_L)
     return record_error(HGL_ERR_INVALID_ARG, "need k >= 1, p >= 0, q >= 0 and k + p <= %d", MAX_L);
@@ -284,70 +293,43 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   if (bp[0] != 0 || bp[nb] != g->n) return record_error(HGL_ERR_INVALID_ARG, "block_ptr must run from 0 to n");
   for (int b = 0; b < nb; ++b)
     if (bp[b + 1] <= bp[b]) return record_error(HGL_ERR_INVALID_ARG, "blocks must be non-empty and increasing");
+  return HGL_OK;
+}
+
+void precond_plan_destroy(PrecondPlan* pl) {
+  if (!pl) return;
+  if (pl->P) hgl_precond_destroy(pl->P);
+  buffer_free(pl->own);
+  delete pl;
+}
+
+// Plan, work space (own buffer if own_space, else the graph's shared one), handle.
+// Synchronous (uploads the block metadata).
+hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* bp, int32_t nb, int32_t k, int32_t p,
+                               int32_t q, int gemm_dtype, bool own_space, cudaStream_t st, PrecondPlan** out) {
+  hgl_graph* g = const_cast<hgl_graph*>(gc);
+  *out = nullptr;
+  HGL_TRY(precond_validate(g, bp, nb, k, p, q, gemm_dtype));
   const int l = k + p;
   const int lpad = (int)rup(l, 16);
-  const int sms = g->num_sms;
-  if (!degrees_ready) HGL_TRY(degrees_launch(g, w, st));
-
-  ProfScope prof(HGL_PROF_RSVD, st);
-  Work wk;
-  HGL_TRY(plan(g, bp, nb, k, l, lpad, gemm_dtype, &wk));
-  HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
-  const bool bf16 = gemm_dtype == HGL_BF16;
-
-  // dense diagonal blocks and the Gaussian start basis
-  if (bf16) {
-    hgl::count_launch(); rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
-                                                            g->csc_idx, g->s, g->t,
-                                                            static_cast<__nv_bfloat16*>(wk.A));
-    hgl::count_launch(); rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<__nv_bfloat16*>(wk.St));
-  } else {
-    hgl::count_launch(); rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
-                                                     g->csc_idx, g->s, g->t, static_cast<double*>(wk.A));
-    hgl::count_launch(); rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, static_cast<double*>(wk.St));
+  PrecondPlan* pl = new (std::nothrow) PrecondPlan();
+  if (!pl) return record_error(HGL_ERR_OOM, "host allocation failed");
+  pl->dtype = gemm_dtype;
+  pl->q = q;
+  hgl_status s_ = plan(g, own_space ? pl->own : g->rsvd, bp, nb, k, l, lpad, gemm_dtype, &pl->wk);
+  if (s_ != HGL_OK) {
+    precond_plan_destroy(pl);
+    return s_;
   }
-  HGL_CHECK_CUDA(cudaGetLastError());
-
-  // Algorithm 1: 1 + 2q products each followed by an orthonormalisation, then W = Theta S
-  const int nprod = 1 + 2 * q;
-  hgl_status s_ = HGL_OK;
-  HGL_LPAD_SWITCH(lpad, {
-    for (int i = 0; i < nprod && s_ == HGL_OK; ++i) {
-      s_ = gemm<LP>(wk, gemm_dtype, sms, st);
-      if (s_ == HGL_OK)
-        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, true)
-                  : cholqr2<double, double, LP>(wk, gemm_dtype, sms, st, true);
-    }
-    if (s_ == HGL_OK) s_ = gemm<LP>(wk, gemm_dtype, sms, st);
-    if (s_ == HGL_OK) {
-      // T = S^T (Theta S), eigendecomposition, Ritz vectors
-      hgl::count_launch();
-      s_ = bf16 ? gram<float, LP>(wk, static_cast<const float*>(wk.Qf), static_cast<const float*>(wk.D), st)
-                : gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
-      if (bf16) {
-        // FP32 rotations: the BF16 products bound the accuracy of T well above FP32's
-        const size_t jsm = 2 * sizeof(float) * LP * LP;
-        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<float, LP>, jsm);
-        if (s_ == HGL_OK) {
-          hgl::count_launch();
-          rsvd::k_jacobi<float, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 16, 1e-10);
-        }
-      } else {
-        const size_t jsm = 2 * sizeof(double) * LP * LP;
-        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
-        if (s_ == HGL_OK) {
-          hgl::count_launch();
-          rsvd::k_jacobi<double, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
-        }
-      }
-    }
-  });
-  HGL_TRY(s_);
-  HGL_CHECK_CUDA(cudaGetLastError());
-
-  // the handle: Q (n x k), gains, eigenvalues, block metadata and 32-row apply tiles
+  const Work& wk = pl->wk;
+  const bool bf16 = gemm_dtype == HGL_BF16;
+  // the handle: Q (n x k), gains, eigenvalues, block metadata and the apply's units
   hgl_precond* P = new (std::nothrow) hgl_precond();
-  if (!P) return record_error(HGL_ERR_OOM, "host allocation failed");
+  if (!P) {
+    precond_plan_destroy(pl);
+    return record_error(HGL_ERR_OOM, "host allocation failed");
+  }
+  pl->P = P;
   P->g = g;
   P->n = g->n;
   P->nb = nb;
@@ -402,7 +384,8 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   const size_t oEt = take(4 * et.size());
   cudaError_t e = cudaMalloc(&P->dev, off);
   if (e != cudaSuccess) {
-    delete P;
+    P->dev = nullptr;
+    precond_plan_destroy(pl);
     return cuda_error(e, "cudaMalloc(preconditioner)", __FILE__, __LINE__);
   }
   char* base = static_cast<char*>(P->dev);
@@ -433,43 +416,141 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   chk(cudaMemcpyAsync(P->blk_slab0, bs0.data(), 4 * bs0.size(), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->exp_block, eb.data(), 4 * eb.size(), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->exp_tile, et.data(), 4 * et.size(), cudaMemcpyHostToDevice, st));
-  const int nu = (int)wk.unit_block.size();
-  if (fin == HGL_OK) {
-    HGL_LPAD_SWITCH(lpad, {
-      if (bf16) {
-        const size_t rs = sizeof(float) * (LP * LP + 128 * (LP + 1));
-        fin = set_smem(rsvd::k_ritz<float, LP>, rs);
-        hgl::count_launch();
-        if (fin == HGL_OK)
-          rsvd::k_ritz<float, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
-              wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const float*>(wk.Qf), wk.R,
-              static_cast<float*>(P->Q));
-      } else {
-        const size_t rs = sizeof(double) * (LP * LP + 128 * (LP + 1));
-        fin = set_smem(rsvd::k_ritz<double, LP>, rs);
-        hgl::count_launch();
-        if (fin == HGL_OK)
-          rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
-              wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R,
-              static_cast<double*>(P->Q));
-      }
-    });
-  }
-  if (fin == HGL_OK) fin = precond_gains_launch(P, wk.ev, lpad, st);
-  if (fin == HGL_OK) {
-    int32_t flags[2] = {0, 0};
-    chk(cudaMemcpyAsync(flags, wk.fail, 8, cudaMemcpyDeviceToHost, st));
-    chk(cudaStreamSynchronize(st));
-    if (fin == HGL_OK && flags[1] != 0)
-      fin = record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
-  }
+  chk(cudaStreamSynchronize(st));  // the host vectors above go out of scope
   if (fin != HGL_OK) {
-    cudaFree(P->dev);
-    delete P;
+    precond_plan_destroy(pl);
     return fin;
   }
-  *out = P;
+  *out = pl;
   return HGL_OK;
 }
 
+// Launches only: Algorithm 1 on every block at the graph's current degrees, the
+// Rayleigh-Ritz vectors and the gains, into the plan's handle.  The Omega seed is
+// `seed`, or *seed_dev when seed_dev is given (read on the device).
+hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t seed, const uint64_t* seed_dev,
+                                cudaStream_t st) {
+  hgl_graph* g = const_cast<hgl_graph*>(gc);
+  Work& wk = pl->wk;
+  hgl_precond* P = pl->P;
+  const int gemm_dtype = pl->dtype;
+  const int q = pl->q;
+  const int nb = wk.B.nb;
+  const int k = wk.B.k;
+  const int lpad = wk.B.lpad;
+  const int sms = g->num_sms;
+  (void)k;
+  ProfScope prof(HGL_PROF_RSVD, st);
+  HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
+  const bool bf16 = gemm_dtype == HGL_BF16;
+
+  // dense diagonal blocks and the Gaussian start basis
+  if (bf16) {
+    hgl::count_launch(2);
+    rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                            g->csc_idx, g->s, g->t,
+                                                            static_cast<__nv_bfloat16*>(wk.A));
+    rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, seed_dev,
+                                                         static_cast<__nv_bfloat16*>(wk.St));
+  } else {
+    hgl::count_launch(2);
+    rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                     g->csc_idx, g->s, g->t, static_cast<double*>(wk.A));
+    rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, seed_dev, static_cast<double*>(wk.St));
+  }
+  HGL_CHECK_CUDA(cudaGetLastError());
+
+  // Algorithm 1: 1 + 2q products each followed by an orthonormalisation, then W = Theta S
+  const int nprod = 1 + 2 * q;
+  hgl_status s_ = HGL_OK;
+  HGL_LPAD_SWITCH(lpad, {
+    for (int i = 0; i < nprod && s_ == HGL_OK; ++i) {
+      s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+      if (s_ == HGL_OK)
+        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, true)
+                  : cholqr2<double, double, LP>(wk, gemm_dtype, sms, st, true);
+    }
+    if (s_ == HGL_OK) s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+    if (s_ == HGL_OK) {
+      // T = S^T (Theta S), eigendecomposition, Ritz vectors
+      s_ = bf16 ? gram<float, LP>(wk, static_cast<const float*>(wk.Qf), static_cast<const float*>(wk.D), st)
+                : gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
+      if (bf16) {
+        // FP32 rotations: the BF16 products bound the accuracy of T well above FP32's
+        const size_t jsm = 2 * sizeof(float) * LP * LP;
+        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<float, LP>, jsm);
+        if (s_ == HGL_OK) {
+          hgl::count_launch();
+          rsvd::k_jacobi<float, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 16, 1e-10);
+        }
+      } else {
+        const size_t jsm = 2 * sizeof(double) * LP * LP;
+        if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
+        if (s_ == HGL_OK) {
+          hgl::count_launch();
+          rsvd::k_jacobi<double, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
+        }
+      }
+    }
+  });
+  HGL_TRY(s_);
+  HGL_CHECK_CUDA(cudaGetLastError());
+
+  const int nu = (int)wk.unit_block.size();
+  HGL_LPAD_SWITCH(lpad, {
+    if (bf16) {
+      const size_t rs = sizeof(float) * (LP * LP + 128 * (LP + 1));
+      s_ = set_smem(rsvd::k_ritz<float, LP>, rs);
+      if (s_ == HGL_OK) {
+        hgl::count_launch();
+        rsvd::k_ritz<float, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
+            wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const float*>(wk.Qf), wk.R,
+            static_cast<float*>(P->Q));
+      }
+    } else {
+      const size_t rs = sizeof(double) * (LP * LP + 128 * (LP + 1));
+      s_ = set_smem(rsvd::k_ritz<double, LP>, rs);
+      if (s_ == HGL_OK) {
+        hgl::count_launch();
+        rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
+            wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R,
+            static_cast<double*>(P->Q));
+      }
+    }
+  });
+  HGL_TRY(s_);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return precond_gains_launch(P, wk.ev, lpad, st);
+}
+
+// The device status words of the last compute: HGL_ERR_TIMEOUT if the tensor-core
+// GEMM gave up a wait.  Synchronises the stream.
+hgl_status precond_plan_check(PrecondPlan* pl, cudaStream_t st) {
+  int32_t flags[2] = {0, 0};
+  HGL_CHECK_CUDA(cudaMemcpyAsync(flags, pl->wk.fail, 8, cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (flags[1] != 0) return record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
+  return HGL_OK;
+}
+
+const hgl_precond* precond_plan_handle(const PrecondPlan* pl) { return pl->P; }
+
+hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const int64_t* bp, int32_t nb, int32_t k,
+                         int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st, hgl_precond** out,
+                         bool degrees_ready) {
+  hgl_graph* g = const_cast<hgl_graph*>(gc);
+  *out = nullptr;
+  HGL_TRY(precond_validate(g, bp, nb, k, p, q, gemm_dtype));
+  if (!degrees_ready) HGL_TRY(degrees_launch(g, w, st));
+  PrecondPlan* pl = nullptr;
+  HGL_TRY(precond_plan_create(g, lam, bp, nb, k, p, q, gemm_dtype, false, st, &pl));
+  hgl_status s_ = precond_plan_compute(g, pl, seed, nullptr, st);
+  if (s_ == HGL_OK) s_ = precond_plan_check(pl, st);
+  if (s_ == HGL_OK) {
+    *out = pl->P;
+    pl->P = nullptr;
+  }
+  precond_plan_destroy(pl);
+  return s_;
+}
 }  // namespace hgl

@@ -195,7 +195,8 @@ __device__ __forceinline__ void omega_pair(int64_t g, int p, uint64_t seed, doub
 // i < rows_b; every other entry (columns j >= lb, padding i) is zero.  One thread per
 // (column pair, basis column).
 template <class TB>
-__global__ void k_omega(Blocks B, uint64_t seed, TB* __restrict__ St) {
+__global__ void k_omega(Blocks B, uint64_t seed_arg, const uint64_t* __restrict__ seed_dev, TB* __restrict__ St) {
+  const uint64_t seed = seed_dev ? *seed_dev : seed_arg;
   const int64_t total = (int64_t)(B.lpad / 2) * B.Ktot;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int p = (int)(q / B.Ktot);

@@ -35,16 +35,30 @@ struct SolverMem {
 // Optional outputs of a solve: in mixed modes the FP32 high part of F (valid until
 // the next solve on the graph).
 struct SolveExtras {
+  // out (mixed modes): the FP32 high part of F, valid until the next solve on the graph
   const float* f32 = nullptr;
   int64_t ld32 = 0;
+  // out: the per-column device state (relres, iterations, breakdown flags)
+  CgState state{};
+  // in: > 0 selects capture mode -- a fixed launch sequence without host reads (one
+  // refinement sweep in mixed modes, this many CG iterations with device-side early
+  // exit); the caller reads the statistics after running it (fill_stats on `state`)
+  int fixed_iters = 0;
 };
 
+// Per-column statistics and the verdict of a finished solve from its device state.
+// Synchronises the stream.
+hgl_status fill_stats(const CgState& S, int c, int refinements, double tol, double* relres_out,
+                      int32_t* iters_out, hgl_solve_stats* stats, cudaStream_t st, hgl_status* verdict);
+
 hgl_status df_split_scalings(const hgl_graph* g, float* s_hi, float* s_lo, float* t_hi, float* t_lo, cudaStream_t st);
+// guard (optional device flag): the kernels return at once when *guard == 0
 hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf, float* Fh, float* Fl, int64_t ld32,
-                       const float* D, cudaStream_t st);
+                       const float* D, cudaStream_t st, const int32_t* guard = nullptr);
 hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
                        const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
-                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows);
+                       double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows,
+                       const int32_t* guard = nullptr);
 
 hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
 
@@ -66,6 +80,20 @@ hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, cons
 // per-column partial sums of A.B for panels of type dt (FP64 or FP32); rows in *rows
 hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,
                             double* partials, cudaStream_t st, int* rows);
+
+// A block rSVD plan for one block layout: created once (allocates, uploads metadata,
+// synchronous), computed any number of times (kernel launches only; capturable), its
+// handle reused by every compute.
+struct PrecondPlan;
+hgl_status precond_plan_create(const hgl_graph* g, double lam, const int64_t* bp, int32_t nb, int32_t k, int32_t p,
+                               int32_t q, int gemm_dtype, bool own_space, cudaStream_t st, PrecondPlan** out);
+hgl_status precond_plan_compute(const hgl_graph* g, PrecondPlan* pl, uint64_t seed, const uint64_t* seed_dev,
+                                cudaStream_t st);
+hgl_status precond_plan_check(PrecondPlan* pl, cudaStream_t st);
+const hgl_precond* precond_plan_handle(const PrecondPlan* pl);
+void precond_plan_destroy(PrecondPlan* pl);
+// Grow the apply's work space for c-column panels of `dt` (so that applies allocate nothing).
+hgl_status precond_reserve(hgl_precond* P, int c, int dt);
 
 hgl_status precond_build(const hgl_graph* g, const double* w, double lam, const int64_t* block_ptr, int32_t nblocks,
                          int32_t k, int32_t p, int32_t q, uint64_t seed, int gemm_dtype, cudaStream_t st,

@@ -5,12 +5,14 @@
 #include <cmath>
 #include <vector>
 
+#include "precond.cuh"
 #include "solver.cuh"
 
 namespace hgl {
 
 hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
                           cudaStream_t st, int max_steps);
+hgl_status project_finish(double* w, int64_t m, double* work, int sms, cudaStream_t st, bool* continued);
 size_t project_work_doubles(int64_t m, int sms);
 
 namespace {
@@ -50,8 +52,8 @@ __global__ void k_step_sums(int64_t m, const double* __restrict__ t, const doubl
 
 }  // namespace
 
-hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, const double* Y, int64_t ldy,
-                              double* F, int64_t ldf, int c, hgl_step_stats* stats, cudaStream_t st) {
+hgl_status adaptive_step_eager(hgl_graph* g, double* w, const hgl_step_opts& o, const double* Y, int64_t ldy,
+                               double* F, int64_t ldf, int c, hgl_step_stats* stats, cudaStream_t st) {
   const int64_t m = g->m;
   const int sms = g->num_sms;
   const int red_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + RED_THREADS - 1) / RED_THREADS, sms * 2));
@@ -109,6 +111,276 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
     stats->dw_norm = std::sqrt(dw2);
   }
   return solve_status;
+}
+
+// ---- captured step (HGL_STEP_GRAPH) -----------------------------------------------
+//
+// The step's launches -- degrees, the block rSVD rebuild (route BR), the solve with a
+// fixed launch sequence (one refinement sweep, a fixed count of CG iterations from
+// which converged columns exit on the device), the gradient, a fixed number of
+// projection steps and the statistics' partial sums -- are captured once into a CUDA
+// graph and replayed by every later call with the same pointers and options.  The
+// Omega seed is read from a device word written before each replay.  The statistics
+// are read after the replay; a projection that had not settled within the fixed steps
+// is finished there.  The graph is captured again if a work buffer it uses has moved.
+
+constexpr int GRAPH_PROJ_STEPS = 48;
+
+struct StepGraph {
+  // the call the graph replays
+  double* w = nullptr;
+  const double* Y = nullptr;
+  int64_t ldy = 0;
+  double* F = nullptr;
+  int64_t ldf = 0;
+  int c = 0;
+  double lam = 0, mu = 0, eta = 0;
+  int route = 0;
+  hgl_solve_opts solve{};
+  std::vector<int64_t> bp;
+  int k = 0, p = 0, q = 0;
+  // resources
+  PrecondPlan* plan = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t* seed_dev = nullptr;
+  std::vector<std::pair<const Buffer*, void*>> deps;
+  std::vector<ProfEvent> prof;
+  unsigned long long launches = 0;
+  // device state read after a replay
+  CgState S{};
+  double* part = nullptr;
+  int red_blocks = 0;
+  double* fpart = nullptr;
+  int frows = 0;
+  double* pwork = nullptr;
+  int fixed_iters = 0;
+
+  bool matches(const double* w_, const hgl_step_opts& o, const double* Y_, int64_t ldy_, const double* F_,
+               int64_t ldf_, int c_) const {
+    if (w_ != w || Y_ != Y || ldy_ != ldy || F_ != F || ldf_ != ldf || c_ != c) return false;
+    if (o.lam != lam || o.mu != mu || o.eta != eta || o.route != route) return false;
+    if (o.solve.tol != solve.tol || o.solve.max_iter != solve.max_iter || o.solve.dtype != solve.dtype ||
+        o.solve.inner_tol != solve.inner_tol || o.solve.max_refine != solve.max_refine ||
+        o.solve.flags != solve.flags)
+      return false;
+    if (route == HGL_ROUTE_BR) {
+      if (o.k != k || o.p != p || o.q != q || o.nblocks + 1 != (int)bp.size()) return false;
+      for (int b = 0; b <= o.nblocks; ++b)
+        if (o.block_ptr[b] != bp[b]) return false;
+    }
+    return true;
+  }
+  bool deps_moved() const {
+    for (const auto& d : deps)
+      if (d.first->ptr != d.second) return true;
+    return false;
+  }
+};
+
+void step_graph_destroy(StepGraph* sg) {
+  if (!sg) return;
+  if (sg->exec) cudaGraphExecDestroy(sg->exec);
+  if (sg->cs) cudaStreamDestroy(sg->cs);
+  if (sg->seed_dev) cudaFree(sg->seed_dev);
+  precond_plan_destroy(sg->plan);
+  prof_graph_release(sg->prof);
+  delete sg;
+}
+
+namespace {
+
+// The launch-only body of a captured step (no host reads, no allocations: every work
+// buffer was sized by the eager call that created the StepGraph).
+hgl_status step_body_captured(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o, cudaStream_t st) {
+  double* w = sg->w;
+  const int c = sg->c;
+  const int64_t m = g->m;
+  const int sms = g->num_sms;
+  const int red_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + RED_THREADS - 1) / RED_THREADS, sms * 2));
+  const size_t pw = project_work_doubles(m, sms);
+  hgl_status stt = HGL_OK;
+  double* buf = static_cast<double*>(buffer_get(g->step, sizeof(double) * (2 * (size_t)m + pw + 3 * red_blocks + 8), &stt));
+  if (!buf) return stt;
+  double* grad = buf;
+  double* w_old = grad + m;
+  double* pwork = w_old + m;
+  double* part = pwork + pw;
+
+  HGL_TRY(degrees_launch(g, w, st));
+  const hgl_precond* P = nullptr;
+  if (sg->route == HGL_ROUTE_BR) {
+    HGL_TRY(precond_plan_compute(g, sg->plan, o.seed, sg->seed_dev, st));
+    P = precond_plan_handle(sg->plan);
+  }
+  hgl_solve_opts so = o.solve;
+  so.flags |= HGL_SOLVE_WARM_START;
+  SolveExtras ext;
+  ext.fixed_iters = sg->fixed_iters;
+  HGL_TRY(cg_solve_impl(g, w, o.lam, o.lam, sg->Y, sg->ldy, sg->F, sg->ldf, c, P, so, nullptr, nullptr, nullptr, st,
+                        true, &ext));
+  if (ext.f32)
+    HGL_TRY(weight_grad_launch(g, w, ext.f32, nullptr, ext.ld32, c, HGL_FP32, o.mu, 0, grad, st));
+  else
+    HGL_TRY(weight_grad_launch(g, w, sg->F, nullptr, sg->ldf, c, HGL_FP64, o.mu, 0, grad, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, GRAPH_PROJ_STEPS));
+  const double* ex = static_cast<const double*>(g->misc.ptr);
+  hgl::count_launch();
+  k_step_sums<<<red_blocks, RED_THREADS, 0, st>>>(m, g->t, ex, w_old, w, part);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  // ||F||^2 partials into the solver's reduction buffer (idle after the solve)
+  double* fpart = static_cast<double*>(g->partials.ptr);
+  int frows = 0;
+  HGL_TRY(panel_dot_launch(g, c, HGL_FP64, sg->F, sg->ldf, sg->F, sg->ldf, fpart, st, &frows));
+  sg->S = ext.state;
+  sg->part = part;
+  sg->red_blocks = red_blocks;
+  sg->fpart = fpart;
+  sg->frows = frows;
+  sg->pwork = pwork;
+  return HGL_OK;
+}
+
+hgl_status step_capture(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o) {
+  if (sg->exec) {
+    cudaGraphExecDestroy(sg->exec);
+    sg->exec = nullptr;
+  }
+  prof_graph_release(sg->prof);
+  const unsigned long long l0 = hgl_launch_count();
+  prof_capture_begin(&sg->prof);
+  HGL_CHECK_CUDA(cudaStreamBeginCapture(sg->cs, cudaStreamCaptureModeThreadLocal));
+  hgl_status body = step_body_captured(g, sg, o, sg->cs);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(sg->cs, &graph);
+  prof_capture_end();
+  sg->launches = hgl_launch_count() - l0;
+  uncount_launch(sg->launches);
+  if (body != HGL_OK || ec != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    prof_graph_release(sg->prof);
+    if (body != HGL_OK) return body;
+    return cuda_error(ec != cudaSuccess ? ec : cudaErrorUnknown, "cudaStreamEndCapture(adaptive step)", __FILE__,
+                      __LINE__);
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&sg->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    sg->exec = nullptr;
+    return cuda_error(ei, "cudaGraphInstantiate(adaptive step)", __FILE__, __LINE__);
+  }
+  sg->deps.clear();
+  for (const Buffer* b : {&g->step, &g->solver, &g->partials, &g->scratch, &g->scratch2, &g->misc})
+    sg->deps.emplace_back(b, b->ptr);
+  if (sg->plan) {
+    hgl_precond* P = const_cast<hgl_precond*>(precond_plan_handle(sg->plan));
+    sg->deps.emplace_back(&P->cbuf, P->cbuf.ptr);
+    sg->deps.emplace_back(&P->pbuf, P->pbuf.ptr);
+  }
+  return HGL_OK;
+}
+
+hgl_status step_replay(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o, hgl_step_stats* stats, cudaStream_t st) {
+  uint64_t seed = o.seed;
+  HGL_CHECK_CUDA(cudaMemcpyAsync(sg->seed_dev, &seed, sizeof(seed), cudaMemcpyHostToDevice, st));
+  HGL_CHECK_CUDA(cudaGraphLaunch(sg->exec, st));
+  count_launch((unsigned)sg->launches);
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  prof_graph_add(sg->prof);
+  if (sg->plan) HGL_TRY(precond_plan_check(sg->plan, st));
+  bool continued = false;
+  HGL_TRY(project_finish(sg->w, g->m, sg->pwork, g->num_sms, st, &continued));
+  if (continued) {
+    // the projection was finished after the replay: recompute the step's sums
+    const double* ex = static_cast<const double*>(g->misc.ptr);
+    const double* w_old = sg->pwork - g->m;
+    hgl::count_launch();
+    k_step_sums<<<sg->red_blocks, RED_THREADS, 0, st>>>(g->m, g->t, ex, w_old, sg->w, sg->part);
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
+  hgl_solve_stats ss{};
+  hgl_status verdict = HGL_OK;
+  const double tol = o.solve.tol > 0 ? o.solve.tol : 1e-10;
+  HGL_TRY(fill_stats(sg->S, sg->c, 0, tol, nullptr, nullptr, &ss, st, &verdict));
+  std::vector<double> hp(3 * (size_t)sg->red_blocks), hf((size_t)sg->frows * sg->c);
+  HGL_CHECK_CUDA(cudaMemcpyAsync(hp.data(), sg->part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(hf.data(), sg->fpart, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  double tr = 0.0, w2 = 0.0, dw2 = 0.0, fnorm2 = 0.0;
+  for (int b = 0; b < sg->red_blocks; ++b) {
+    tr += hp[3 * b];
+    w2 += hp[3 * b + 1];
+    dw2 += hp[3 * b + 2];
+  }
+  for (double x : hf) fnorm2 += x;
+  if (stats) {
+    stats->solve = ss;
+    stats->objective = fnorm2 - tr + o.mu * w2;
+    stats->dw_norm = std::sqrt(dw2);
+  }
+  return verdict;
+}
+
+}  // namespace
+
+hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, const double* Y, int64_t ldy,
+                              double* F, int64_t ldf, int c, hgl_step_stats* stats, cudaStream_t st) {
+  if (!(o.flags & HGL_STEP_GRAPH)) return adaptive_step_eager(g, w, o, Y, ldy, F, ldf, c, stats, st);
+  if (o.solve.dtype != HGL_FP64 && o.solve.dtype != HGL_FP32)
+    return record_error(HGL_ERR_INVALID_ARG, "a captured step takes FP64 or FP32 solves");
+  StepGraph*& sg = g->step_graph;
+  if (!sg || !sg->matches(w, o, Y, ldy, F, ldf, c)) {
+    // a new call pattern: run it eagerly (which also sizes every work buffer the graph
+    // will use), then set up the graph's own resources; the next call captures
+    step_graph_destroy(sg);
+    sg = nullptr;
+    const hgl_status s = adaptive_step_eager(g, w, o, Y, ldy, F, ldf, c, stats, st);
+    if (s != HGL_OK && s != HGL_ERR_NOT_CONVERGED) return s;
+    StepGraph* ng = new (std::nothrow) StepGraph();
+    if (!ng) return record_error(HGL_ERR_OOM, "host allocation failed");
+    ng->w = w;
+    ng->Y = Y;
+    ng->ldy = ldy;
+    ng->F = F;
+    ng->ldf = ldf;
+    ng->c = c;
+    ng->lam = o.lam;
+    ng->mu = o.mu;
+    ng->eta = o.eta;
+    ng->route = o.route;
+    ng->solve = o.solve;
+    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-7;
+    ng->fixed_iters = cg_iteration_bound(o.lam, o.solve.dtype == HGL_FP64 ? (o.solve.tol > 0 ? o.solve.tol : 1e-10)
+                                                                           : floor) + 4;
+    hgl_status e = HGL_OK;
+    if (o.route == HGL_ROUTE_BR) {
+      ng->bp.assign(o.block_ptr, o.block_ptr + o.nblocks + 1);
+      ng->k = o.k;
+      ng->p = o.p;
+      ng->q = o.q;
+      e = precond_plan_create(g, o.lam, o.block_ptr, o.nblocks, o.k, o.p, o.q, HGL_BF16, true, st, &ng->plan);
+      if (e == HGL_OK)
+        e = precond_reserve(const_cast<hgl_precond*>(precond_plan_handle(ng->plan)), c, o.solve.dtype);
+    }
+    if (e == HGL_OK) {
+      const cudaError_t ce = cudaMalloc(&ng->seed_dev, sizeof(uint64_t));
+      if (ce != cudaSuccess) e = cuda_error(ce, "cudaMalloc(seed word)", __FILE__, __LINE__);
+    }
+    if (e == HGL_OK) {
+      const cudaError_t ce = cudaStreamCreateWithFlags(&ng->cs, cudaStreamNonBlocking);
+      if (ce != cudaSuccess) e = cuda_error(ce, "cudaStreamCreate(capture)", __FILE__, __LINE__);
+    }
+    if (e != HGL_OK) {
+      step_graph_destroy(ng);
+      return e;
+    }
+    sg = ng;
+    return s;
+  }
+  if (!sg->exec || sg->deps_moved()) HGL_TRY(step_capture(g, sg, o));
+  return step_replay(g, sg, o, stats, st);
 }
 
 }  // namespace hgl

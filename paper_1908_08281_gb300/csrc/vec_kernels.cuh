@@ -28,6 +28,8 @@ struct CgState {
   int32_t* bad;    // non-finite or breakdown seen in column j
   int32_t* run_flag;
   unsigned* done;  // last-block counter of k_cg_reduce
+  int32_t* need;   // captured solves: 1 while a refinement sweep is needed (k_inner_targets)
+  const int32_t* guard = nullptr;  // RED_RESID: skip the reduction when *guard == 0
 };
 
 enum ReduceMode : int {
@@ -224,6 +226,7 @@ k_cg_reduce(const double* __restrict__ pa, const double* __restrict__ pb, int ro
   const int c = S.c;
   const int j = blockIdx.x * 8 + wid;
   if (MODE != RED_B2 && MODE != RED_INIT && MODE != RED_RESID && *S.run_flag == 0) return;
+  if (MODE == RED_RESID && S.guard && *S.guard == 0) return;
   if (j < c) {
     double a = 0.0, b = 0.0;
     for (int r = lane; r < rows; r += 32) {
@@ -242,7 +245,6 @@ k_cg_reduce(const double* __restrict__ pa, const double* __restrict__ pb, int ro
         const double rz = pb ? b : a;
         S.rr[j] = a;
         S.rz[j] = rz;
-        S.iters[j] = 0;
         const bool finite = isfinite(a) && isfinite(rz);
         if (!finite) S.bad[j] = 1;
         S.active[j] = (finite && S.b2[j] > 0.0 && a > S.target[j]) ? 1 : 0;

@@ -423,7 +423,11 @@ hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, 
     for (int k = 0; k < batch; ++k) { hgl::count_launch(); k_proj_step<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps_sum, ps_cnt, ps); }
     HGL_CHECK_CUDA(cudaGetLastError());
     steps += batch;
-    if (max_steps > 0 && steps >= max_steps) break;
+    if (max_steps > 0) {
+      // a fixed number of steps (capturable: no host reads; converged steps return at once)
+      if (steps >= max_steps) break;
+      continue;
+    }
     int32_t done = 0;
     HGL_CHECK_CUDA(cudaMemcpyAsync(&done, &ps->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     HGL_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -431,6 +435,36 @@ hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, 
   }
   hgl::count_launch(); k_proj_apply<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps, w);
   HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
+// After a projection launched with a fixed number of steps: if its iteration had not
+// settled, continue it (host-checked batches) from the state in `work` and apply the
+// final threshold again.  Synchronises the stream.
+hgl_status project_finish(double* w, int64_t m, double* work, int sms, cudaStream_t st, bool* continued) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
+  double* v = work;
+  double* ps_sum = v + m;
+  double* ps_cnt = ps_sum + blocks;
+  ProjState* ps = reinterpret_cast<ProjState*>(ps_cnt + blocks);
+  int32_t done = 0;
+  HGL_CHECK_CUDA(cudaMemcpyAsync(&done, &ps->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  *continued = !done;
+  if (done) return HGL_OK;
+  for (int64_t steps = 0; !done && steps <= m + 16; steps += 16) {
+    for (int k = 0; k < 16; ++k) {
+      hgl::count_launch();
+      k_proj_step<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps_sum, ps_cnt, ps);
+    }
+    HGL_CHECK_CUDA(cudaGetLastError());
+    HGL_CHECK_CUDA(cudaMemcpyAsync(&done, &ps->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  hgl::count_launch();
+  k_proj_apply<<<blocks, PROJ_THREADS, 0, st>>>(v, m, ps, w);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   return HGL_OK;
 }
 

@@ -211,3 +211,52 @@ def test_precond_apply_fp32_matches_definition(k, c):
     # reproducible: fixed summation order
     Z2 = hgl.precond_apply(Pc, R32).to(torch.float64).cpu().numpy()
     assert np.array_equal(Z, Z2)
+
+
+@pytest.mark.parametrize("route,dtype,tol", [(hgl.HGL_ROUTE_BR, hgl.HGL_FP32, 1e-8),
+                                             (hgl.HGL_ROUTE_CG, hgl.HGL_FP64, 1e-10)])
+def test_captured_step_matches_oracle_each_step(route, dtype, tol):
+    """HGL_STEP_GRAPH: the first call runs eagerly, the second captures the step into a
+    CUDA graph, later calls replay it.  Every step is checked against the oracle from
+    the GPU's own w: the solve (error bound of the tolerance), the projected weights and
+    the reported objective and step length."""
+    wl, d, H, w, g = _setup(n=6000, m=10000, c=8, seed=12)
+    bp = d["block_ptr"]
+    mu, eta = 1e-3, 2e-3
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    launches = []
+    for i in range(5):
+        w_before = wt.cpu().numpy().copy()
+        l0 = hgl.launch_count()
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, mu, eta, tol=tol, dtype=dtype, route=route, block_ptr=bp,
+                               k=16, p=8, q=2, seed=SEED + i, flags=hgl.HGL_STEP_GRAPH)
+        launches.append(hgl.launch_count() - l0)
+        assert st.solve.relres_max <= tol, (i, st.solve.relres_max)
+        Fg = F.cpu().numpy()
+        Fr, _ = core.certified_solve(H, w_before, wl.lam, d["Y"])
+        err = np.linalg.norm(Fg - Fr, axis=0) / np.linalg.norm(Fr, axis=0)
+        assert err.max() <= (1 + wl.lam) / wl.lam * tol * 1.01 + 1e-13, (i, err.max())
+        w_ref = core.project_simplex(w_before - eta * core.weight_grad(H, w_before, Fr, mu))
+        w_new = wt.cpu().numpy()
+        assert np.linalg.norm(w_new - w_ref) <= 1e-4 * np.linalg.norm(w_ref), i
+        assert abs(w_new.sum() - 1.0) <= 1e-12 and w_new.min() >= 0.0
+        assert np.isclose(st.objective, core.objective(H, w_before, Fg, mu), rtol=1e-6), i
+        assert np.isclose(st.dw_norm, np.linalg.norm(w_new - w_before), rtol=1e-9, atol=1e-15), i
+    # replays launch what the capture recorded: the same count every step
+    assert launches[2] == launches[3] == launches[4] > 0
+    # a different panel (new pointer) starts a new graph without error
+    F2 = hgl.padded_panel(d["n"], d["c"])
+    F2.copy_(F)
+    st = hgl.adaptive_step(g, wt, Y, F2, wl.lam, mu, eta, tol=tol, dtype=dtype, route=route, block_ptr=bp,
+                           k=16, p=8, q=2, seed=SEED + 9, flags=hgl.HGL_STEP_GRAPH)
+    assert st.solve.relres_max <= tol
+
+
+def test_captured_step_rejects_bf16_panels():
+    wl, d, H, w, g = _setup(n=600, m=900, c=2, seed=13)
+    wt = torch.tensor(d["w0"], device=DEV)
+    with pytest.raises(hgl.HglError):
+        hgl.adaptive_step(g, wt, _panel(d["Y"]), hgl.padded_panel(d["n"], d["c"]), wl.lam, 0.0, 1e-3,
+                          dtype=hgl.HGL_BF16, flags=hgl.HGL_STEP_GRAPH)
