@@ -54,10 +54,10 @@ VecGrid vec_grid(const hgl_graph* g, int c, int elt) {
 
 template <class TA, class TB>
 hgl_status panel_dot(const hgl_graph* g, int c, const TA* A, int64_t lda, const TB* B, int64_t ldb, double scale,
-                     double* partials, cudaStream_t st, int* rows) {
+                     double* partials, cudaStream_t st, int* rows, const int32_t* run_flag = nullptr) {
   VecGrid vg = vec_grid(g, c, sizeof(TA));
   dim3 grid(vg.gx, vg.gy);
-  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_dot<TA, TB, LG><<<grid, VEC_THREADS, 0, st>>>(g->n, c, A, lda, B, ldb, scale, partials))));
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_dot<TA, TB, LG><<<grid, VEC_THREADS, 0, st>>>(g->n, c, A, lda, B, ldb, scale, partials, run_flag))));
   HGL_CHECK_CUDA(cudaGetLastError());
   *rows = vg.gx;
   return HGL_OK;
@@ -65,10 +65,10 @@ hgl_status panel_dot(const hgl_graph* g, int c, const TA* A, int64_t lda, const 
 
 template <class TX, class TZ, bool DOT>
 hgl_status panel_scale(const hgl_graph* g, int c, const TX* X, int64_t ldx, double scale, TZ* Z, int64_t ldz,
-                       double* partials, cudaStream_t st, int* rows) {
+                       double* partials, cudaStream_t st, int* rows, const int32_t* run_flag = nullptr) {
   VecGrid vg = vec_grid(g, c, sizeof(TZ));
   dim3 grid(vg.gx, vg.gy);
-  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_scale<TX, TZ, LG, DOT><<<grid, VEC_THREADS, 0, st>>>(g->n, c, X, ldx, scale, Z, ldz, partials))));
+  HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch(); HGL_LG_SWITCH(vg.lg, (k_panel_scale<TX, TZ, LG, DOT><<<grid, VEC_THREADS, 0, st>>>(g->n, c, X, ldx, scale, Z, ldz, partials, run_flag))));
   HGL_CHECK_CUDA(cudaGetLastError());
   if (rows) *rows = vg.gx;
   return HGL_OK;
@@ -428,7 +428,13 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
     hgl::count_launch();
     k_inner_targets<<<(c + 255) / 256, 256, 0, st>>>(S, tol, floor);
     HGL_CHECK_CUDA(cudaGetLastError());
-    HGL_CHECK_CUDA(cudaMemset2DAsync(X32, sizeof(float) * sm.ld32, 0, sizeof(float) * c, g->n, st));
+    if (guarded) {
+      HGL_PROFILED(HGL_PROF_VECTOR, hgl::count_launch();
+                   k_zero_panel<<<g->num_sms * 8, 256, 0, st>>>(g->n, c, X32, sm.ld32, guard));
+      HGL_CHECK_CUDA(cudaGetLastError());
+    } else {
+      HGL_CHECK_CUDA(cudaMemset2DAsync(X32, sizeof(float) * sm.ld32, 0, sizeof(float) * c, g->n, st));
+    }
     int rows_b = 0;
     const float* zsrc = R32;
     if (P) {
@@ -437,13 +443,16 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
     }
     if (mode == HGL_BF16) {
       HGL_TRY((panel_scale<float, bf16_t, false>(g, c, zsrc, sm.ld32, 1.0, static_cast<bf16_t*>(sm.P), sm.ld16,
-                                                 nullptr, st, nullptr)));
+                                                 nullptr, st, nullptr, guard)));
+    } else if (guarded) {
+      HGL_TRY((panel_scale<float, float, false>(g, c, zsrc, sm.ld32, 1.0, static_cast<float*>(sm.P), sm.ld32,
+                                                nullptr, st, nullptr, guard)));
     } else {
       HGL_CHECK_CUDA(cudaMemcpy2DAsync(sm.P, sizeof(float) * sm.ld32, zsrc, sizeof(float) * sm.ld32,
                                        sizeof(float) * c, g->n, cudaMemcpyDeviceToDevice, st));
     }
     int drows = 0;
-    HGL_TRY((panel_dot<float, float>(g, c, R32, sm.ld32, R32, sm.ld32, 1.0, sm.pa, st, &drows)));
+    HGL_TRY((panel_dot<float, float>(g, c, R32, sm.ld32, R32, sm.ld32, 1.0, sm.pa, st, &drows, guard)));
     if (P && rows_b != drows) {
       const int mx = std::max(drows, rows_b);
       if (drows < mx)
@@ -476,12 +485,12 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
 
   if (extras && extras->fixed_iters > 0) {
     // capture mode: a fixed launch sequence without host reads -- the residual, then two
-    // guarded sweeps each followed by a guarded residual.  A sweep aims at
-    // max(floor, 0.1 tol / relres); one FP32 sweep reaches about 1e-7 times the starting
-    // relres, so the second runs (on the device's decision) only when the first fell
-    // short.  Statistics stay on the device.
+    // guarded sweeps (the first two of the eager loop) each followed by a guarded
+    // residual; the second runs, on the device's decision, only when the first fell
+    // short of tol (one FP32 sweep reaches about 1e-7 times the starting relres and at
+    // most the inner floor).  Statistics stay on the device.
     if (mode == HGL_BF16) return record_error(HGL_ERR_INVALID_ARG, "captured solves take FP64 or FP32 panels");
-    const double floor = o.inner_tol > 0 ? o.inner_tol : 1e-7;
+    const double floor = inner_tol;
     int done = 0;
     HGL_TRY(residual(nullptr));
     for (int sw = 0; sw < 2; ++sw) {
@@ -524,11 +533,13 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
 }
 
 hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,
-                            double* partials, cudaStream_t st, int* rows) {
+                            double* partials, cudaStream_t st, int* rows, const int32_t* run_flag) {
   if (dt == HGL_FP64)
-    return panel_dot<double, double>(g, c, (const double*)A, lda, (const double*)B, ldb, 1.0, partials, st, rows);
+    return panel_dot<double, double>(g, c, (const double*)A, lda, (const double*)B, ldb, 1.0, partials, st, rows,
+                                     run_flag);
   if (dt == HGL_FP32)
-    return panel_dot<float, float>(g, c, (const float*)A, lda, (const float*)B, ldb, 1.0, partials, st, rows);
+    return panel_dot<float, float>(g, c, (const float*)A, lda, (const float*)B, ldb, 1.0, partials, st, rows,
+                                   run_flag);
   return record_error(HGL_ERR_INVALID_ARG, "dot panels must be FP64 or FP32");
 }
 

@@ -517,7 +517,7 @@ hgl_status precond_apply_launch(const hgl_precond* Pc, const hgl_graph* g, const
   } else {
     return record_error(HGL_ERR_INVALID_ARG, "preconditioner panels must be FP64 or FP32");
   }
-  if (partials_rz) HGL_TRY(panel_dot_launch(g, c, dt, R, ldr, Z, ldz, partials_rz, st, rows));
+  if (partials_rz) HGL_TRY(panel_dot_launch(g, c, dt, R, ldr, Z, ldz, partials_rz, st, rows, run_flag));
   return HGL_OK;
 }
 

@@ -79,7 +79,7 @@ hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, cons
 
 // per-column partial sums of A.B for panels of type dt (FP64 or FP32); rows in *rows
 hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, int64_t lda, const void* B, int64_t ldb,
-                            double* partials, cudaStream_t st, int* rows);
+                            double* partials, cudaStream_t st, int* rows, const int32_t* run_flag = nullptr);
 
 // A block rSVD plan for one block layout: created once (allocates, uploads metadata,
 // synchronous), computed any number of times (kernel launches only; capturable), its

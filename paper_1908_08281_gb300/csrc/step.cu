@@ -303,7 +303,12 @@ hgl_status step_replay(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o, hgl_
   hgl_solve_stats ss{};
   hgl_status verdict = HGL_OK;
   const double tol = o.solve.tol > 0 ? o.solve.tol : 1e-10;
+  // a mixed-precision solve ran its second sweep when the flag is still set
+  int32_t need = 0;
+  if (sg->solve.dtype != HGL_FP64)
+    HGL_CHECK_CUDA(cudaMemcpyAsync(&need, sg->S.need, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   HGL_TRY(fill_stats(sg->S, sg->c, 0, tol, nullptr, nullptr, &ss, st, &verdict));
+  ss.refinements = need;
   std::vector<double> hp(3 * (size_t)sg->red_blocks), hf((size_t)sg->frows * sg->c);
   HGL_CHECK_CUDA(cudaMemcpyAsync(hp.data(), sg->part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, st));
   HGL_CHECK_CUDA(cudaMemcpyAsync(hf.data(), sg->fpart, sizeof(double) * hf.size(), cudaMemcpyDeviceToHost, st));
@@ -351,7 +356,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
     ng->eta = o.eta;
     ng->route = o.route;
     ng->solve = o.solve;
-    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-7;
+    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-5;
     ng->fixed_iters = cg_iteration_bound(o.lam, o.solve.dtype == HGL_FP64 ? (o.solve.tol > 0 ? o.solve.tol : 1e-10)
                                                                            : floor) + 4;
     hgl_status e = HGL_OK;

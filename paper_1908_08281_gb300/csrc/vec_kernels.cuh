@@ -70,7 +70,8 @@ __device__ __forceinline__ void block_col_partials(const double (&v)[E], int col
 template <class TA, class TB, int LG>
 __global__ void __launch_bounds__(VEC_THREADS)
 k_panel_dot(int64_t n, int c, const TA* __restrict__ A, int64_t lda, const TB* __restrict__ B, int64_t ldb,
-            double scale, double* __restrict__ partials) {
+            double scale, double* __restrict__ partials, const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
   using L = VecLayout<TA, LG>;
   constexpr int E = L::E;
   using Acc = typename AccOf<TA>::type;
@@ -98,7 +99,8 @@ k_panel_dot(int64_t n, int c, const TA* __restrict__ A, int64_t lda, const TB* _
 template <class TX, class TZ, int LG, bool DOT>
 __global__ void __launch_bounds__(VEC_THREADS)
 k_panel_scale(int64_t n, int c, const TX* __restrict__ X, int64_t ldx, double scale, TZ* __restrict__ Z,
-              int64_t ldz, double* __restrict__ partials) {
+              int64_t ldz, double* __restrict__ partials, const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
   using L = VecLayout<TZ, LG>;
   constexpr int E = L::E;
   using Acc = typename AccOf<TX>::type;
@@ -214,6 +216,17 @@ k_add_correction(int64_t n, int c, const TD* __restrict__ D, int64_t ldd, double
     for (int j = 0; j < E; ++j) f[j] += d[j];
     vstore<double, double, E>(F + r * ldf + col, f, c - col);
   }
+}
+
+// Z[r, 0 : round4(c)] = 0 for FP32 panels with ldz a multiple of 4 (internal panels:
+// their padding columns are zeroed too); returns at once when *run_flag == 0.
+static __global__ void k_zero_panel(int64_t n, int c, float* __restrict__ Z, int64_t ldz,
+                             const int32_t* __restrict__ run_flag) {
+  if (run_flag && *run_flag == 0) return;
+  const int vecs = (c + 3) / 4;
+  const int64_t total = n * vecs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    *reinterpret_cast<float4*>(Z + (q / vecs) * ldz + (q % vecs) * 4) = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Per-column reduction of [rows x c] partials and the scalar CG logic of column j.
