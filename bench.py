@@ -38,6 +38,11 @@ METRIC = "adaptive outer iterations/sec (rel err <= 1e-5)"
 UNIT = "iters/s"
 TOL = 3e-6          # relative residual; kappa(M) <= 3 at lam = 0.5 -> relative error <= 9e-6
 SEED = 20190822
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel family on
+# the full workload at a given column chunk, from one ncu capture of this bench
+# (profiles/operator_apply_full_adaptive.md, profiles/pair_residual_full_adaptive.md);
+# reported as roofline.traffic only for a run of that workload with that chunk.
+NCU_TRAFFIC_PER_LAUNCH = {("operator", 128): 66.0e9, ("residual", 128): 149.2e9}
 LOOP = 20           # outer iterations of one adaptive loop
 K_RANK, P_OVER, Q_ITERS = 64, 10, 2
 
@@ -364,7 +369,7 @@ def main():
                     hgl.PROF_GRADIENT: "weight gradient (k_grad_edge + k_grad_vertex + k_grad_final), FP32"}
     lpad = ((K_RANK + P_OVER + 15) // 16) * 16
     op_chunk = (tuned or {}).get("operator_chunk_fp32") or 128
-    pair_chunk = (tuned or {}).get("residual_chunk") or 256
+    pair_chunk = (tuned or {}).get("residual_chunk") or 128
     per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4, -(-c // op_chunk)),
                         hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, -(-c // pair_chunk)),
                         hgl.PROF_GEMM: bytes_gemm(bp, lpad),
@@ -392,8 +397,10 @@ def main():
     dcnt = min(executed.get(dom, dcnt), dcnt)
     davg = dms / max(dcnt, 1)
     achieved = per_launch_bytes[dom] / (davg / 1000.0) / 1e9
+    fam_key = {hgl.PROF_OPERATOR: ("operator", op_chunk), hgl.PROF_RESIDUAL: ("residual", pair_chunk)}.get(dom)
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get(fam_key) if (args.scale == 1.0 and fam_key) else None
     roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_launch": per_launch_bytes[dom], "ms_per_launch": davg, "launches": dcnt}
     if prof[hgl.PROF_GEMM][1] > 0:
         gavg = prof[hgl.PROF_GEMM][0] / prof[hgl.PROF_GEMM][1]
