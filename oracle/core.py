@@ -71,6 +71,58 @@ def theta_apply(H: sp.spmatrix, w: np.ndarray, X: np.ndarray, a: float = 0.0,
     return a * X + b * Z
 
 
+def incidence_lists(n: int, m: int, edge_ptr, members):
+    """Hyperedge -> members and vertex -> hyperedges lists (CSR-like arrays) built on the
+    host from the input member lists: (edge_ptr, members, vert_ptr, vert_edges)."""
+    edge_ptr = np.asarray(edge_ptr, dtype=np.int64)
+    members = np.asarray(members, dtype=np.int64)
+    edge_of = np.repeat(np.arange(m, dtype=np.int64), np.diff(edge_ptr))
+    order = np.argsort(members, kind="stable")
+    vert_edges = edge_of[order]
+    vert_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(members, minlength=n), out=vert_ptr[1:])
+    return edge_ptr, members, vert_ptr, vert_edges
+
+
+def _dv_all(lists, w) -> np.ndarray:
+    """dv = H w for every vertex (Section 2), summed over each vertex's hyperedge list."""
+    edge_ptr, members, vert_ptr, vert_edges = lists
+    n = vert_ptr.size - 1
+    return np.bincount(np.repeat(np.arange(n), np.diff(vert_ptr)), weights=np.asarray(w)[vert_edges], minlength=n)
+
+
+def theta_rows(lists, w, X_rows, rows, a: float = 0.0, b: float = 1.0) -> np.ndarray:
+    """Rows `rows` of Z = a X + b Theta X evaluated one by one from Eq. 1:
+        Z_v = a X_v + b s_v sum_{e ni v} (w_e / de_e) sum_{u in e} s_u X_u,
+        s_u = (sum_{e' ni u} w_e')^-1/2 (0 where that sum is 0).
+    `lists` is ``incidence_lists``; X_rows(u) returns the rows u of X (float64 array).
+    For large graphs where only a few outputs can be checked."""
+    edge_ptr, members, vert_ptr, vert_edges = lists
+    w = np.asarray(w, dtype=np.float64)
+    dv_all = _dv_all(lists, w)
+
+    def s_of(u):
+        dv = dv_all[np.asarray(u)]
+        out = np.zeros_like(dv)
+        out[dv > 0] = 1.0 / np.sqrt(dv[dv > 0])
+        return out
+
+    out = []
+    for v in rows:
+        sv = s_of([v])[0]
+        acc = None
+        for e in vert_edges[vert_ptr[v]:vert_ptr[v + 1]]:
+            mem = members[edge_ptr[e]:edge_ptr[e + 1]]
+            part = (s_of(mem)[:, None] * X_rows(mem)).sum(axis=0) * (w[e] / mem.size)
+            acc = part if acc is None else acc + part
+        xv = X_rows(np.array([v]))[0]
+        z = a * xv
+        if acc is not None:
+            z = z + b * sv * acc
+        out.append(z)
+    return np.array(out)
+
+
 def system_dense(H: sp.spmatrix, w: np.ndarray, lam: float) -> np.ndarray:
     """M = (1 + lam) I - Theta; M F = lam Y is Eq. 6 multiplied by (1 + lam)."""
     Th = theta_dense(H, w)
@@ -209,6 +261,43 @@ def bilinear_theta_grad(H, w, F, Z, dv_frozen: bool = False) -> np.ndarray:
     inv_dv[dv > 0] = 1.0 / dv[dv > 0]
     per_vertex = inv_dv * ((G * UZ).sum(axis=1) + (R * UF).sum(axis=1))
     return explicit - 0.5 * (H.T @ per_vertex)
+
+
+def weight_grad_entries(lists, w, F_rows, edges, mu: float) -> np.ndarray:
+    """Entries `edges` of grad_w P(w) = -d tr(F^T Theta F)/dw + 2 mu w (Eq. 4 at fixed F,
+    dv(w) included), evaluated hyperedge by hyperedge for large graphs:
+        d/dw_e tr(F^T Theta F) = ||sF_e||^2 / de_e - sum_{v in e} <G_v, UF_v> / dv_v,
+    G = Dv^-1/2 F, sF_e = sum_{u in e} G_u, UF_v = sum_{e' ni v} (w_e'/de_e') sF_e'.
+    `lists` is ``incidence_lists``; F_rows(u) returns the rows u of F (float64)."""
+    edge_ptr, members, vert_ptr, vert_edges = lists
+    w = np.asarray(w, dtype=np.float64)
+    dv_all = _dv_all(lists, w)
+
+    def dv_of(u):
+        return dv_all[np.asarray(u)]
+
+    def g_rows(u):
+        dv = dv_of(u)
+        s = np.zeros_like(dv)
+        s[dv > 0] = 1.0 / np.sqrt(dv[dv > 0])
+        return s[:, None] * F_rows(u), dv
+
+    def sF(e):
+        return g_rows(members[edge_ptr[e]:edge_ptr[e + 1]])[0].sum(axis=0)
+
+    out = []
+    for e in edges:
+        mem = members[edge_ptr[e]:edge_ptr[e + 1]]
+        se = sF(e)
+        val = float(se @ se) / mem.size
+        G, dv = g_rows(mem)
+        for i, v in enumerate(mem):
+            if dv[i] <= 0:
+                continue
+            UF = sum((w[f] / (edge_ptr[f + 1] - edge_ptr[f])) * sF(f) for f in vert_edges[vert_ptr[v]:vert_ptr[v + 1]])
+            val -= float(G[i] @ UF) / dv[i]
+        out.append(-val + 2.0 * mu * w[e])
+    return np.array(out)
 
 
 def weight_grad(H, w, F, mu: float, dv_frozen: bool = False) -> np.ndarray:

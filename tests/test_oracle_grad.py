@@ -126,3 +126,20 @@ def test_adaptive_loop_descends_objective():
     w_prev = trace[-2]["w_new"]
     assert np.allclose(theta_apply(H, w_prev, F, 2.0, -1.0), Y, atol=1e-8)
     assert np.array_equal(w, trace[-1]["w_new"])
+
+
+def test_weight_grad_entries_match_the_full_gradient():
+    """Entry-by-entry evaluation of the Eq. 4 gradient (for sampled checks at full
+    size) against the sparse-product gradient, with a zero-degree vertex."""
+    from oracle.core import incidence_lists, weight_grad_entries
+    rng = np.random.default_rng(8)
+    n, m = 30, 25
+    ptr, mem = tiny_hypergraph(rng, n, m, 2, 6)
+    H = incidence_matrix(build_incidence(n, m, ptr, mem))
+    w = rng.random(m) + 0.1
+    w[np.asarray(H[4].nonzero()[1])] = 0.0
+    F = rng.standard_normal((n, 4))
+    lists = incidence_lists(n, m, ptr, mem)
+    edges = np.arange(m)
+    g = weight_grad_entries(lists, w, lambda u: F[np.asarray(u)], edges, 1e-3)
+    assert np.allclose(g, weight_grad(H, w, F, 1e-3), rtol=1e-12, atol=1e-14)

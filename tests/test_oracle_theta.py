@@ -144,3 +144,24 @@ def test_paper_form_equivalence():
     lam = 0.7
     X = np.eye(10) - theta_dense(H, w) / (1 + lam)
     assert np.allclose(system_dense(H, w, lam), (1 + lam) * X, atol=1e-15)
+
+
+def test_theta_rows_matches_the_sparse_operator():
+    """Row-by-row evaluation of Eq. 1 (for checking sampled outputs of large graphs)
+    against the factor-by-factor sparse operator, including a zero-degree vertex."""
+    import numpy as np
+    from oracle.core import incidence_lists, theta_apply, theta_rows
+    from oracle.incidence import build_incidence, incidence_matrix
+    from tests._util import tiny_hypergraph
+    rng = np.random.default_rng(5)
+    n, m = 40, 30
+    ptr, mem = tiny_hypergraph(rng, n, m, 2, 7)
+    H = incidence_matrix(build_incidence(n, m, ptr, mem))
+    w = rng.random(m) + 0.1
+    w[np.asarray(H[3].nonzero()[1])] = 0.0  # vertex 3 loses all weight
+    X = rng.standard_normal((n, 5))
+    lists = incidence_lists(n, m, ptr, mem)
+    rows = np.array([0, 3, 7, 39])
+    Z = theta_rows(lists, w, lambda u: X[np.asarray(u)], rows, 1.5, -1.0)
+    ref = theta_apply(H, w, X, 1.5, -1.0)[rows]
+    assert np.allclose(Z, ref, rtol=1e-13, atol=1e-14)
