@@ -35,6 +35,9 @@ int device_sm_count();
 int resident_blocks(const void* fn, int threads, size_t smem);
 
 constexpr int TUNE_PAIR = 7;
+// tune_key(TUNE_GRID + panel kind, c) -> grid policy of the operator's gather passes:
+// 1 = eight blocks per SM (several waves), otherwise the blocks resident at once
+constexpr int TUNE_GRID = 16;
 inline uint64_t tune_key(int kind, int c) { return ((uint64_t)kind << 32) | (uint32_t)c; }
 // Tuned chunk in vectors for (kind, c), or 0.
 inline int tuned_chunk_vecs(const hgl_graph* g, int kind, int c);

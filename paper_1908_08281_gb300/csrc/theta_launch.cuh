@@ -58,6 +58,8 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   using A = typename AccOf<TX>::type;
   const A* sA = scal_s<A>(g);
   const A* tA = scal_t<A>(g);
+  const bool eight_per_sm = tuned_chunk_vecs(g, TUNE_GRID + cl.xdt, cl.c) == 1;
+  auto per_sm = [&](const void* fn) { return eight_per_sm ? 8 : resident_blocks(fn, OP_THREADS, 0); };
   ProfScope prof(HGL_PROF_OPERATOR, st);
   const TX* X = static_cast<const TX*>(cl.X);
   TZ* Z = static_cast<TZ*>(cl.Z);
@@ -66,7 +68,7 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
 #define HGL_EDGE_CASE(LG_, NV_)                                                                        \
   else if (lg == LG_ && nv == NV_) {                                                                   \
     auto fn = k_edge_pass<TX, TT, LG_, NV_>;                                                           \
-    const int gr = edge_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));    \
+    const int gr = edge_grid(g, per_sm(reinterpret_cast<const void*>(fn)));    \
     hgl::count_launch();                                                                               \
     fn<<<gr, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, sA, tA, X,   \
                                   cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);                       \
@@ -74,7 +76,7 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
 #define HGL_VERTEX_CASE(LG_, NV_)                                                                      \
   else if (lg == LG_ && nv == NV_) {                                                                   \
     auto fn = k_vertex_pass<TX, TT, TZ, LG_, NV_, EPI>;                                                \
-    grid2 = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));         \
+    grid2 = vertex_grid(g, per_sm(reinterpret_cast<const void*>(fn)));         \
     hgl::count_launch();                                                                               \
     fn<<<grid2, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, sA, Tp, (int64_t)cc, X, cl.ldx, Z,  \
                                      cl.ldz, c0, cw, cl.c, cl.a, cl.b, cl.Y, cl.ldy, cl.gy, cl.partials, \
@@ -83,7 +85,7 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
 #define HGL_EDGE_ROWS(LG_)                                                                             \
   else if (lg == LG_) {                                                                                \
     auto fn = k_edge_rows<TX, TT, LG_>;                                                                \
-    const int gr = edge_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));    \
+    const int gr = edge_grid(g, per_sm(reinterpret_cast<const void*>(fn)));    \
     hgl::count_launch();                                                                               \
     fn<<<gr, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy, sA, tA, X,   \
                                   cl.ldx, c0, cw, Tp, (int64_t)cc, cl.run_flag);                       \
@@ -91,7 +93,7 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
 #define HGL_VERTEX_ROWS(LG_)                                                                           \
   else if (lg == LG_) {                                                                                \
     auto fn = k_vertex_rows<TX, TT, TZ, LG_, EPI>;                                                     \
-    grid2 = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));         \
+    grid2 = vertex_grid(g, per_sm(reinterpret_cast<const void*>(fn)));         \
     hgl::count_launch();                                                                               \
     fn<<<grid2, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, sA, Tp, (int64_t)cc, X, cl.ldx, Z,  \
                                      cl.ldz, c0, cw, cl.c, cl.a, cl.b, cl.Y, cl.ldy, cl.gy, cl.partials, \

@@ -90,6 +90,27 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
   }
   g->tuned_chunk[tune_key(dtype, c)] = best;
   if (chunk_cols) *chunk_cols = best * E;
+  // grid policy at that chunk: the blocks resident at once (one wave) or eight per SM
+  {
+    OpCall cl{};
+    cl.g = g;
+    cl.xdt = dtype;
+    cl.zdt = dtype;
+    cl.X = X.p;
+    cl.ldx = ld;
+    cl.Z = Z.p;
+    cl.ldz = ld;
+    cl.c = c;
+    cl.a = 1.5;
+    cl.b = -1.0;
+    cl.epi = EPI_PLAIN;
+    float ms[2] = {0.f, 0.f};
+    for (int pol = 0; pol < 2; ++pol) {
+      g->tuned_chunk[tune_key(TUNE_GRID + dtype, c)] = pol;
+      HGL_TRY(time_ms(st, [&] { return op_launch(cl, st, nullptr); }, &ms[pol]));
+    }
+    g->tuned_chunk[tune_key(TUNE_GRID + dtype, c)] = ms[1] < ms[0] ? 1 : 0;
+  }
 
   // pair-arithmetic residual (used by the FP32 / BF16 solvers): 4-float vectors
   if (dtype != HGL_FP64) {
