@@ -387,6 +387,25 @@ def project_simplex(v: np.ndarray) -> np.ndarray:
     return np.maximum(v - tau, 0.0)
 
 
+def active_set_step(w, g, eta: float) -> np.ndarray:
+    """The steepest-descent step of Eq. 5 read literally.  Active constraints: G_1
+    (1^T w = 1, always active) and G_j (w_e = 0) for every weight already at 0.  Their
+    multipliers make the direction nabla S = nabla P + c_1 1 + sum_j c_j e_j vanish on the
+    pinned weights and sum to zero over the free ones:
+        d_e = g_e - mean_{free}(g)  (w_e > 0),   d_e = 0  (w_e = 0).
+    w - eta d is clamped at 0 (weights that cross 0 join the pinned set) and rescaled to
+    sum 1.  With no free weight, or nothing left after clamping, w is returned unchanged."""
+    w = np.asarray(w, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    free = w > 0
+    if not free.any():
+        return w.copy()
+    d = np.where(free, g - g[free].mean(), 0.0)
+    v = np.where(free, np.maximum(w - eta * d, 0.0), 0.0)
+    total = v.sum()
+    return v / total if total > 0 else w.copy()
+
+
 def simplex_threshold(v: np.ndarray) -> float:
     """The tau of ``project_simplex``."""
     v = np.asarray(v, dtype=np.float64)

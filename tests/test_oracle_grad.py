@@ -143,3 +143,47 @@ def test_weight_grad_entries_match_the_full_gradient():
     edges = np.arange(m)
     g = weight_grad_entries(lists, w, lambda u: F[np.asarray(u)], edges, 1e-3)
     assert np.allclose(g, weight_grad(H, w, F, 1e-3), rtol=1e-12, atol=1e-14)
+
+
+def test_active_set_step_hand_example():
+    """w = (0.5, 0.3, 0.2, 0), g = (1, 0, -1, 5): the pinned fourth weight stays 0, the
+    free mean of g is 0.  eta = 0.1: (0.4, 0.3, 0.3, 0), already on the simplex.
+    eta = 0.6: (-0.1, 0.3, 0.8, 0) clamps to (0, 0.3, 0.8, 0), sum 1.1, rescaled to
+    (0, 3/11, 8/11, 0)."""
+    from oracle.core import active_set_step
+    w = np.array([0.5, 0.3, 0.2, 0.0])
+    g = np.array([1.0, 0.0, -1.0, 5.0])
+    assert np.allclose(active_set_step(w, g, 0.1), [0.4, 0.3, 0.3, 0.0], rtol=0, atol=1e-15)
+    assert np.allclose(active_set_step(w, g, 0.6), [0.0, 3 / 11, 8 / 11, 0.0], rtol=0, atol=1e-15)
+    # nothing free: unchanged
+    assert np.array_equal(active_set_step(np.zeros(3), np.ones(3), 1.0), np.zeros(3))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_active_set_step_equals_projection_without_clamping(seed):
+    """Inside the simplex with a step too small to reach 0, both readings of Eq. 5 give
+    w - eta (g - mean g): the active-set step and the Euclidean projection agree."""
+    from oracle.core import active_set_step
+    rng = np.random.default_rng(seed)
+    w = rng.random(50) + 0.5
+    w /= w.sum()
+    g = rng.standard_normal(50)
+    eta = 0.1 * w.min() / np.abs(g).max()
+    assert np.allclose(active_set_step(w, g, eta), project_simplex(w - eta * g), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_active_set_step_feasible_pinned_and_descending(seed):
+    from oracle.core import active_set_step
+    rng = np.random.default_rng(10 + seed)
+    w = rng.random(200)
+    w[rng.random(200) < 0.3] = 0.0
+    w /= w.sum()
+    g = rng.standard_normal(200)
+    for eta in (1e-4, 1e-2, 1.0):
+        wn = active_set_step(w, g, eta)
+        assert wn.min() >= 0.0 and abs(wn.sum() - 1.0) <= 1e-12
+        assert (wn[w == 0] == 0).all()
+    # first order: the direction is a descent direction of <g, .> on the simplex
+    wn = active_set_step(w, g, 1e-6)
+    assert g @ (wn - w) < 0
