@@ -331,6 +331,18 @@ hgl_status hgl_weight_grad(const hgl_graph* g, const double* w, const void* F,
  *   w          device FP64[m], in/out;  grad device FP64[m] (NULL = zero)
  * Asynchronous.
  */
+/*
+ * hgl_active_set_step -- the steepest-descent step of Eq. 5 read literally: the
+ * constraint 1^T w = 1 is always active and w_e = 0 is active for every weight already
+ * at 0; their multipliers make the step vanish on the pinned weights and sum to zero
+ * over the free ones, d_e = grad_e - mean over free of grad; w - eta d is clamped at 0
+ * (weights that cross 0 join the pinned set) and rescaled to sum 1.  With no free
+ * weight, or none left after clamping, w is unchanged.  w device FP64[m] in/out, grad
+ * device FP64[m].  Fixed-order reductions (reproducible); allocates its work space
+ * stream-ordered.  Asynchronous.
+ */
+hgl_status hgl_active_set_step(double* w, const double* grad, double eta, int64_t m, void* stream);
+
 hgl_status hgl_project_simplex(double* w, const double* grad, double eta, int64_t m,
                                void* stream);
 
@@ -370,7 +382,9 @@ hgl_status hgl_adjoint_grad(hgl_graph* g, const double* w, double lam, const dou
 #define HGL_ROUTE_CG 0   /* plain CG solve (CG-ITH-HWEG, Section 4)                     */
 #define HGL_ROUTE_BR 1   /* CG preconditioned by the block rSVD (BR-ITH-HWEG)          */
 
-#define HGL_STEP_GRAPH 1 /* replay the step as one captured CUDA graph                 */
+#define HGL_STEP_GRAPH      1 /* replay the step as one captured CUDA graph            */
+#define HGL_STEP_ACTIVE_SET 2 /* weight step by hgl_active_set_step instead of the     */
+                              /* Euclidean projection (hgl_project_simplex)            */
 
 typedef struct {
   double  lam;           /* ranking regulariser (theta of Eq. 3), > 0                     */

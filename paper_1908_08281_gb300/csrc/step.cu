@@ -14,6 +14,16 @@ hgl_status project_launch(double* w, const double* grad, double eta, int64_t m, 
                           cudaStream_t st, int max_steps);
 hgl_status project_finish(double* w, int64_t m, double* work, int sms, cudaStream_t st, bool* continued);
 size_t project_work_doubles(int64_t m, int sms);
+hgl_status active_set_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
+                             cudaStream_t st);
+size_t active_set_work_doubles(int64_t m, int sms);
+
+namespace {
+// work of the weight step: the projection's or the active-set step's, whichever is larger
+size_t step_work_doubles(int64_t m, int sms) {
+  return std::max(project_work_doubles(m, sms), active_set_work_doubles(m, sms));
+}
+}  // namespace
 
 namespace {
 
@@ -58,7 +68,7 @@ hgl_status adaptive_step_eager(hgl_graph* g, double* w, const hgl_step_opts& o, 
   const int sms = g->num_sms;
   const int red_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + RED_THREADS - 1) / RED_THREADS, sms * 2));
   // step buffer: grad[m] | w_old[m] | projection work | sums
-  const size_t pw = project_work_doubles(m, sms);
+  const size_t pw = step_work_doubles(m, sms);
   hgl_status stt = HGL_OK;
   // misc is used by the gradient (ex, phi); the step keeps its vectors in `step`
   double* buf = static_cast<double*>(buffer_get(g->step, sizeof(double) * (2 * (size_t)m + pw + 3 * red_blocks + 8), &stt));
@@ -90,7 +100,10 @@ hgl_status adaptive_step_eager(hgl_graph* g, double* w, const hgl_step_opts& o, 
     HGL_TRY(weight_grad_launch(g, w, F, nullptr, ldf, c, HGL_FP64, o.mu, 0, grad, st));
   // ||F||^2 for the objective
   HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-  HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, 0));
+  if (o.flags & HGL_STEP_ACTIVE_SET)
+    HGL_TRY(active_set_launch(w, grad, o.eta, m, pwork, sms, st));
+  else
+    HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, 0));
   const double* ex = static_cast<const double*>(g->misc.ptr);
   hgl::count_launch(); k_step_sums<<<red_blocks, RED_THREADS, 0, st>>>(m, g->t, ex, w_old, w, part);
   HGL_CHECK_CUDA(cudaGetLastError());
@@ -136,6 +149,7 @@ struct StepGraph {
   int c = 0;
   double lam = 0, mu = 0, eta = 0;
   int route = 0;
+  int flags = 0;
   hgl_solve_opts solve{};
   std::vector<int64_t> bp;
   int k = 0, p = 0, q = 0;
@@ -159,7 +173,7 @@ struct StepGraph {
   bool matches(const double* w_, const hgl_step_opts& o, const double* Y_, int64_t ldy_, const double* F_,
                int64_t ldf_, int c_) const {
     if (w_ != w || Y_ != Y || ldy_ != ldy || F_ != F || ldf_ != ldf || c_ != c) return false;
-    if (o.lam != lam || o.mu != mu || o.eta != eta || o.route != route) return false;
+    if (o.lam != lam || o.mu != mu || o.eta != eta || o.route != route || o.flags != flags) return false;
     if (o.solve.tol != solve.tol || o.solve.max_iter != solve.max_iter || o.solve.dtype != solve.dtype ||
         o.solve.inner_tol != solve.inner_tol || o.solve.max_refine != solve.max_refine ||
         o.solve.flags != solve.flags)
@@ -198,7 +212,7 @@ hgl_status step_body_captured(hgl_graph* g, StepGraph* sg, const hgl_step_opts& 
   const int64_t m = g->m;
   const int sms = g->num_sms;
   const int red_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + RED_THREADS - 1) / RED_THREADS, sms * 2));
-  const size_t pw = project_work_doubles(m, sms);
+  const size_t pw = step_work_doubles(m, sms);
   hgl_status stt = HGL_OK;
   double* buf = static_cast<double*>(buffer_get(g->step, sizeof(double) * (2 * (size_t)m + pw + 3 * red_blocks + 8), &stt));
   if (!buf) return stt;
@@ -224,7 +238,10 @@ hgl_status step_body_captured(hgl_graph* g, StepGraph* sg, const hgl_step_opts& 
   else
     HGL_TRY(weight_grad_launch(g, w, sg->F, nullptr, sg->ldf, c, HGL_FP64, o.mu, 0, grad, st));
   HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-  HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, GRAPH_PROJ_STEPS));
+  if (o.flags & HGL_STEP_ACTIVE_SET)
+    HGL_TRY(active_set_launch(w, grad, o.eta, m, pwork, sms, st));
+  else
+    HGL_TRY(project_launch(w, grad, o.eta, m, pwork, sms, st, GRAPH_PROJ_STEPS));
   const double* ex = static_cast<const double*>(g->misc.ptr);
   hgl::count_launch();
   k_step_sums<<<red_blocks, RED_THREADS, 0, st>>>(m, g->t, ex, w_old, w, part);
@@ -291,7 +308,7 @@ hgl_status step_replay(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o, hgl_
   prof_graph_add(sg->prof);
   if (sg->plan) HGL_TRY(precond_plan_check(sg->plan, st));
   bool continued = false;
-  HGL_TRY(project_finish(sg->w, g->m, sg->pwork, g->num_sms, st, &continued));
+  if (!(o.flags & HGL_STEP_ACTIVE_SET)) HGL_TRY(project_finish(sg->w, g->m, sg->pwork, g->num_sms, st, &continued));
   if (continued) {
     // the projection was finished after the replay: recompute the step's sums
     const double* ex = static_cast<const double*>(g->misc.ptr);
@@ -355,6 +372,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
     ng->mu = o.mu;
     ng->eta = o.eta;
     ng->route = o.route;
+    ng->flags = o.flags;
     ng->solve = o.solve;
     const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-5;
     ng->fixed_iters = cg_iteration_bound(o.lam, o.solve.dtype == HGL_FP64 ? (o.solve.tol > 0 ? o.solve.tol : 1e-10)

@@ -386,6 +386,94 @@ __global__ void k_proj_apply(const double* __restrict__ v, int64_t m, const Proj
   }
 }
 
+// ---- active-set steepest descent (Eq. 5 read literally) --------------------------
+// Pinned weights (w_e = 0) stay 0; free ones move by -eta (g_e - mean over free of g),
+// are clamped at 0 and rescaled to sum 1.  Three launches, block reductions in a fixed
+// order (every block re-adds the previous kernel's partials in index order), no host
+// reads.  work layout: v[m] | stats[2 * blocks] | sums[blocks]
+
+__device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[PROJ_THREADS / 32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int i = 0; i < PROJ_THREADS / 32; ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+  }
+}
+
+__global__ void k_as_stats(const double* __restrict__ w, const double* __restrict__ g, int64_t m,
+                           double* __restrict__ stats) {
+  __shared__ double red[2][PROJ_THREADS / 32];
+  double s = 0.0, cnt = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    if (w[e] > 0.0) {
+      s += g[e];
+      cnt += 1.0;
+    }
+  block_sum2(s, cnt, red);
+  if (threadIdx.x == 0) {
+    stats[2 * blockIdx.x] = s;
+    stats[2 * blockIdx.x + 1] = cnt;
+  }
+}
+
+__global__ void k_as_update(const double* __restrict__ w, const double* __restrict__ g, double eta, int64_t m,
+                            const double* __restrict__ stats, double* __restrict__ v, double* __restrict__ sums) {
+  __shared__ double red[2][PROJ_THREADS / 32];
+  __shared__ double mean_s, cnt_s;
+  if (threadIdx.x == 0) {
+    double s = 0.0, c = 0.0;
+    for (unsigned i = 0; i < gridDim.x; ++i) {
+      s += stats[2 * i];
+      c += stats[2 * i + 1];
+    }
+    mean_s = c > 0.0 ? s / c : 0.0;
+    cnt_s = c;
+  }
+  __syncthreads();
+  const double mean = mean_s;
+  double tot = 0.0, unused = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+    const double we = w[e];
+    double x = 0.0;
+    if (we > 0.0) {
+      x = we - eta * (g[e] - mean);
+      x = x > 0.0 ? x : 0.0;
+    }
+    v[e] = x;
+    tot += x;
+  }
+  block_sum2(tot, unused, red);
+  if (threadIdx.x == 0) sums[blockIdx.x] = cnt_s > 0.0 ? tot : 0.0;
+}
+
+__global__ void k_as_scale(double* __restrict__ w, const double* __restrict__ v, int64_t m,
+                           const double* __restrict__ sums) {
+  __shared__ double total_s;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned i = 0; i < gridDim.x; ++i) t += sums[i];
+    total_s = t;
+  }
+  __syncthreads();
+  const double total = total_s;
+  if (!(total > 0.0)) return;  // nothing free, or nothing left after clamping: w unchanged
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    w[e] = v[e] / total;
+}
+
 }  // namespace
 
 hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
@@ -468,6 +556,26 @@ hgl_status project_finish(double* w, int64_t m, double* work, int sms, cudaStrea
   return HGL_OK;
 }
 
+size_t active_set_work_doubles(int64_t m, int sms) {
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
+  return (size_t)(m + 3 * blocks + 4);
+}
+
+hgl_status active_set_launch(double* w, const double* grad, double eta, int64_t m, double* work, int sms,
+                             cudaStream_t st) {
+  ProfScope prof(HGL_PROF_PROJECT, st);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
+  double* v = work;
+  double* stats = v + m;
+  double* sums = stats + 2 * blocks;
+  hgl::count_launch(3);
+  k_as_stats<<<blocks, PROJ_THREADS, 0, st>>>(w, grad, m, stats);
+  k_as_update<<<blocks, PROJ_THREADS, 0, st>>>(w, grad, eta, m, stats, v, sums);
+  k_as_scale<<<blocks, PROJ_THREADS, 0, st>>>(w, v, m, sums);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
 size_t project_work_doubles(int64_t m, int sms) {
   const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((m + PROJ_THREADS - 1) / PROJ_THREADS, sms * 2));
   return (size_t)(m + 2 * blocks + 4);
@@ -488,6 +596,18 @@ extern "C" hgl_status hgl_weight_grad(const hgl_graph* g, const double* w, const
   hgl_graph* gg = const_cast<hgl_graph*>(g);
   HGL_TRY(hgl::degrees_launch(gg, w, st));
   return hgl::weight_grad_launch(gg, w, F, Z, ld, c, dtype, mu, flags, grad, st);
+}
+
+extern "C" hgl_status hgl_active_set_step(double* w, const double* grad, double eta, int64_t m, void* stream) {
+  if (!w || !grad || m < 1) return hgl::record_error(HGL_ERR_INVALID_ARG, "w or grad is NULL, or m < 1");
+  if (!(eta >= 0.0)) return hgl::record_error(HGL_ERR_INVALID_ARG, "eta must be >= 0");
+  cudaStream_t st = hgl::as_stream(stream);
+  const int sms = hgl::device_sm_count();
+  double* work = nullptr;
+  HGL_CHECK_CUDA(cudaMallocAsync(&work, sizeof(double) * hgl::active_set_work_doubles(m, sms), st));
+  hgl_status s = hgl::active_set_launch(w, grad, eta, m, work, sms, st);
+  cudaFreeAsync(work, st);
+  return s;
 }
 
 extern "C" hgl_status hgl_project_simplex(double* w, const double* grad, double eta, int64_t m, void* stream) {

@@ -23,6 +23,7 @@ HGL_SOLVE_WARM_START = 1
 HGL_GRAD_DV_FROZEN = 1
 HGL_ROUTE_CG, HGL_ROUTE_BR = 0, 1
 HGL_STEP_GRAPH = 1
+HGL_STEP_ACTIVE_SET = 2
 
 STATUS = {
     0: "HGL_OK", -1: "HGL_ERR_INVALID_ARG", -2: "HGL_ERR_INDEX_RANGE", -3: "HGL_ERR_DUPLICATE_MEMBER",
@@ -88,6 +89,7 @@ _SIGNATURES = {
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
+    "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_adjoint_grad": (_I32, [_P, _P, _D, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P,
                                 ctypes.POINTER(SolveStats), _P]),
     "hgl_adaptive_step": (_I32, [_P, _P, ctypes.POINTER(StepOpts), _P, _I64, _P, _I64, _I32,
@@ -405,6 +407,12 @@ def adjoint_grad(g: Graph, w: torch.Tensor, lam: float, F: torch.Tensor, G: torc
     if st != 0 and (raise_on_fail or st not in (-7,)):
         _check(st)
     return grad, Z, stats
+
+
+def active_set_step(w: torch.Tensor, grad: torch.Tensor, eta: float, stream=None) -> torch.Tensor:
+    """In place: the active-set steepest-descent step of Eq. 5 (pinned zeros stay 0)."""
+    _check(lib().hgl_active_set_step(_vec(w, "w"), _vec(grad, "grad"), eta, w.numel(), _stream(stream)))
+    return w
 
 
 def project_simplex(w: torch.Tensor, grad: torch.Tensor | None, eta: float, stream=None) -> torch.Tensor:

@@ -291,6 +291,46 @@ def test_project_simplex(m, scale):
     assert abs(out.sum() - 1) < 1e-10 and out.min() >= 0
 
 
+@pytest.mark.parametrize("m,frac0,eta", [(1, 0.0, 1.0), (9, 0.3, 0.05), (5000, 0.2, 1e-4), (5000, 0.2, 1e-1),
+                                         (300_000, 0.5, 1e-6), (300_000, 0.0, 1e-3)])
+def test_active_set_step(m, frac0, eta):
+    """The literal active-set step of Eq. 5 against the oracle: pinned zeros, clamping
+    at 0 and rescaling (large eta), and the unclamped regime (small eta)."""
+    rng = np.random.default_rng(m + int(100 * frac0))
+    w = rng.random(m)
+    w[rng.random(m) < frac0] = 0.0
+    if w.sum() == 0:
+        w[0] = 1.0
+    w /= w.sum()
+    gvec = rng.standard_normal(m)
+    wt = torch.tensor(w, device=DEV)
+    hgl.active_set_step(wt, torch.tensor(gvec, device=DEV), eta)
+    ref = core.active_set_step(w, gvec, eta)
+    out = wt.cpu().numpy()
+    assert np.allclose(out, ref, rtol=1e-12, atol=1e-15)
+    assert abs(out.sum() - 1) < 1e-12 and out.min() >= 0 and (out[w == 0] == 0).all()
+
+
+@pytest.mark.parametrize("flags", [hgl.HGL_STEP_ACTIVE_SET, hgl.HGL_STEP_ACTIVE_SET | hgl.HGL_STEP_GRAPH])
+def test_adaptive_loop_active_set_step(flags):
+    """Outer iterations with the active-set weight step (eager and captured), each step
+    checked against the oracle from the GPU's own w."""
+    wl, d, og, H = _case("small_fp64", 1)
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    eta = 1e-3
+    for i in range(5):
+        w_before = wt.cpu().numpy().copy()
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 1e-3, eta, tol=1e-10, flags=flags)
+        assert st.solve.relres_max <= 1e-10
+        Fr = core.solve_dense(H, w_before, wl.lam, d["Y"])
+        assert _relcol(F.cpu().numpy(), Fr).max() <= 1e-9
+        w_ref = core.active_set_step(w_before, core.weight_grad(H, w_before, Fr, 1e-3), eta)
+        assert np.linalg.norm(wt.cpu().numpy() - w_ref) <= 1e-9 * np.linalg.norm(w_ref), i
+
+
 # ------------------------------------------------------------- adaptive step ---
 
 def test_adaptive_loop_small_workload():
