@@ -87,7 +87,10 @@ uint64_t hgl_launch_count(void);
                               /* CholeskyQR2, Jacobi, Ritz vectors)                     */
 #define HGL_PROF_VECTOR   6   /* CG vector updates and panel dot products/copies        */
 #define HGL_PROF_PROJECT  7   /* simplex projection                                     */
-#define HGL_PROF_FAMILIES 8
+#define HGL_PROF_OPRESID  8   /* residual from one operator pass with the residual      */
+                              /* epilogue (FP32 estimate of the mixed solvers, FP64     */
+                              /* residual of the FP64 solver)                           */
+#define HGL_PROF_FAMILIES 9
 hgl_status hgl_profile_enable(int32_t on);
 hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches);
 
@@ -188,8 +191,8 @@ hgl_status hgl_apply_theta_noalloc(const hgl_graph* g, const double* w, double a
  * The paper has no counterpart: the chunk trades one long burst per gathered row
  * against re-reading the index arrays once per chunk, and the best width depends on
  * n, m, c, the panel type and the degree distribution.  At the chosen chunk it also
- * times the grid of the gather passes (the blocks resident at once, one wave, or
- * eight blocks per SM).  The choices are stored in the graph and used by every later
+ * times the grid of the gather passes with the CG's epilogue (the blocks resident at
+ * once, one wave, or eight blocks per SM; eight only when more than 3% faster).  The choices are stored in the graph and used by every later
  * call with the same (dtype, c); untuned graphs use a 128-column chunk and one-wave
  * grids.  Results of later calls may differ from untuned ones in summation
  * order only (each column's sums are unchanged for the operator; the pair residual
@@ -198,10 +201,13 @@ hgl_status hgl_apply_theta_noalloc(const hgl_graph* g, const double* w, double a
  *   w               device FP64[m] weights (sets the graph's degree vectors)
  *   chunk_cols      optional host out: the chosen operator chunk in columns
  *   pair_chunk_cols optional host out: the chosen residual chunk (0 for FP64)
+ *   grid_policy     optional host out: the chosen grid (0 = one wave of resident
+ *                   blocks, 1 = eight blocks per SM)
  * Synchronises `stream`.
  */
 hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c, hgl_dtype dtype,
-                             int32_t* chunk_cols, int32_t* pair_chunk_cols, void* stream);
+                             int32_t* chunk_cols, int32_t* pair_chunk_cols, int32_t* grid_policy,
+                             void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Solve (Eq. 6 by conjugate gradient, Eqs. 16-20)                           */

@@ -19,6 +19,14 @@ namespace hgl {
 constexpr int OP_THREADS = 256;
 constexpr int OP_WARPS = OP_THREADS / 32;
 
+// z + gy y of the residual epilogue: in FP64 for FP64 accumulators, in FP32 for FP32
+// ones (an FP32 residual is an estimate: its rounding, a few units of 2^-24 of |lam Y|,
+// is far above FP64's, and FP64 arithmetic would slow the pass several-fold).
+__device__ __forceinline__ double resid_add(double z, double gy, double y) { return z + gy * y; }
+__device__ __forceinline__ float resid_add(float z, double gy, double y) {
+  return __fmaf_rn((float)gy, (float)y, z);
+}
+
 // Hyperedges are visited in decreasing size order (`order`).  The first `nheavy` of
 // them (more than HEAVY_ROW members) get one thread block each: the block's warps
 // split the member list and their partial sums are added in warp order through
@@ -253,7 +261,7 @@ k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
             const int nv = cw - col < E ? cw - col : E;
             for (int j = 0; j < E; ++j) y[j] = j < nv ? Y[v * ldy + c0 + col + j] : 0.0;
 #pragma unroll
-            for (int j = 0; j < E; ++j) z[j] = (A)((double)z[j] + gy * y[j]);
+            for (int j = 0; j < E; ++j) z[j] = resid_add(z[j], gy, y[j]);
           }
           const int nvalid = cw - col;
           vstore<TZ, A, E>(Z + v * ldz + c0 + col, z, nvalid);
@@ -420,7 +428,7 @@ k_vertex_rows(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
         const int nv = cw - col < E ? cw - col : E;
         for (int j = 0; j < E; ++j) y[j] = j < nv ? Y[v * ldy + c0 + col + j] : 0.0;
 #pragma unroll
-        for (int j = 0; j < E; ++j) z[j] = (A)((double)z[j] + gy * y[j]);
+        for (int j = 0; j < E; ++j) z[j] = resid_add(z[j], gy, y[j]);
       }
       vstore<TZ, A, E>(Z + v * ldz + c0 + col, z, cw - col);
       if constexpr (EPI == EPI_DOT_XZ) {

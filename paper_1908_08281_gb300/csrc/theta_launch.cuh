@@ -60,7 +60,7 @@ hgl_status op_launch_typed(const OpCall& cl, cudaStream_t st, int* grid2_out) {
   const A* tA = scal_t<A>(g);
   const bool eight_per_sm = tuned_chunk_vecs(g, TUNE_GRID + cl.xdt, cl.c) == 1;
   auto per_sm = [&](const void* fn) { return eight_per_sm ? 8 : resident_blocks(fn, OP_THREADS, 0); };
-  ProfScope prof(HGL_PROF_OPERATOR, st);
+  ProfScope prof(cl.epi == EPI_RESID ? HGL_PROF_OPRESID : HGL_PROF_OPERATOR, st);
   const TX* X = static_cast<const TX*>(cl.X);
   TZ* Z = static_cast<TZ*>(cl.Z);
   for (int c0 = 0; c0 < cl.c; c0 += cc) {

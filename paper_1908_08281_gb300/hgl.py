@@ -79,7 +79,8 @@ _SIGNATURES = {
     "hgl_degrees": (_I32, [_P, _P, _P, _P, _P, _P]),
     "hgl_apply_theta": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_apply_theta_noalloc": (_I32, [_P, _P, _D, _D, _P, _I64, _P, _I64, _I32, _I32, _P]),
-    "hgl_tune_operator": (_I32, [_P, _P, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
+    "hgl_tune_operator": (_I32, [_P, _P, _I32, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                 ctypes.POINTER(_I32), _P]),
     "hgl_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P, _P,
                             ctypes.POINTER(SolveStats), _P]),
     "hgl_block_rsvd": (_I32, [_P, _P, _D, ctypes.POINTER(_I64), _I32, _I32, _I32, _I32, _U64, _I32, _P,
@@ -120,10 +121,10 @@ def launch_count() -> int:
 
 
 PROF_OPERATOR, PROF_RESIDUAL, PROF_GEMM, PROF_GRADIENT = 0, 1, 2, 3
-PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT = 4, 5, 6, 7
+PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT, PROF_OPRESID = 4, 5, 6, 7, 8
 PROF_NAMES = {0: "operator apply", 1: "pair-arithmetic residual", 2: "grouped block GEMM (tcgen05)",
               3: "weight gradient", 4: "preconditioner apply", 5: "block rSVD build (all)",
-              6: "CG vector kernels", 7: "simplex projection"}
+              6: "CG vector kernels", 7: "simplex projection", 8: "residual by one operator pass"}
 
 
 def profile_enable(on: bool = True):
@@ -301,15 +302,18 @@ def apply_theta_noalloc(g: Graph, w: torch.Tensor, X: torch.Tensor, Z: torch.Ten
     return Z
 
 
-def tune_operator(g: Graph, w: torch.Tensor, c: int, dtype: int = HGL_FP64, stream=None) -> tuple[int, int]:
+def tune_operator(g: Graph, w: torch.Tensor, c: int, dtype: int = HGL_FP64,
+                  stream=None) -> tuple[int, int, int]:
     """Time the supported column chunks of the operator (and, for FP32/BF16, of the
-    pair residual) on this graph for c-column panels; the graph keeps the fastest.
-    Returns (operator chunk, residual chunk) in columns."""
+    pair residual) on this graph for c-column panels, then the grid of its gather
+    passes; the graph keeps the fastest.  Returns (operator chunk, residual chunk) in
+    columns and the grid policy (0 = one wave of resident blocks, 1 = eight per SM)."""
     op = ctypes.c_int32(0)
     pair = ctypes.c_int32(0)
+    grid = ctypes.c_int32(0)
     _check(lib().hgl_tune_operator(g.handle, _vec(w, "w"), c, dtype, ctypes.byref(op), ctypes.byref(pair),
-                                   _stream(stream)))
-    return op.value, pair.value
+                                   ctypes.byref(grid), _stream(stream)))
+    return op.value, pair.value, grid.value
 
 
 def cg_solve(g: Graph, w: torch.Tensor, lam: float, Y: torch.Tensor, F: torch.Tensor | None = None,

@@ -152,7 +152,8 @@ def test_tuned_operator_and_residual_still_match(dtype, ch):
     w /= w.sum()
     g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
     wt = torch.tensor(w, device=DEV)
-    op_cc, pair_cc = hgl.tune_operator(g, wt, c, dtype)
+    op_cc, pair_cc, grid = hgl.tune_operator(g, wt, c, dtype)
+    assert grid in (0, 1)
     E = 16 // torch.tensor([], dtype=ch).element_size()
     assert 1 <= op_cc and (op_cc % E == 0 or op_cc >= c)
     if dtype == hgl.HGL_FP64:
@@ -208,6 +209,34 @@ def test_cg_mixed_precision(mode):
     assert st.relres_max <= 1e-8
     # kappa(M) <= (1+lam)/lam bounds the error by the residual
     assert err.max() <= (1 + wl.lam) / wl.lam * 1e-8 * 1.01 + 1e-12
+
+
+def test_cg_fp32_loose_tol_starts_from_fp32_residual():
+    """At tol >= 4 * 2^-24 * (1 + 2(1+lam)/lam) the FP32 solve starts from an FP32
+    estimate of the first residual; convergence is still decided on the FP64-accurate
+    residual: the reported relres matches the host's FP64 residual of the returned F,
+    and a warm start from a converged F ends without iterations (the estimate alone
+    never ends a solve)."""
+    wl, d, og, H = _case("mixed_cg", 4, n=9000, m=14000, c=21)
+    tol = 3e-6
+    assert tol >= 4 * 2.0 ** -24 * (1 + 2 * (1 + wl.lam) / wl.lam)
+    w = np.random.default_rng(5).random(d["m"]) + 0.1
+    w /= w.sum()
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    wt = torch.tensor(w, device=DEV)
+    Y = _panel(d["Y"])
+    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=tol, dtype=hgl.HGL_FP32)
+    Fg = F.cpu().numpy()
+    R = wl.lam * d["Y"] - core.theta_apply(H, w, Fg, 1.0 + wl.lam, -1.0)
+    rel = np.linalg.norm(R, axis=0) / np.linalg.norm(wl.lam * d["Y"], axis=0)
+    assert rel.max() <= tol, rel.max()
+    assert np.allclose(relres.cpu().numpy(), rel, rtol=1e-3, atol=1e-12)
+    ref, _ = core.certified_solve(H, w, wl.lam, d["Y"])
+    assert _relcol(Fg, ref).max() <= (1 + wl.lam) / wl.lam * tol * 1.01
+    F2, relres2, iters2, st2 = hgl.cg_solve(g, wt, wl.lam, Y, F=F, tol=tol, dtype=hgl.HGL_FP32, warm_start=True)
+    assert iters2.cpu().numpy().max() == 0 and st2.refinements == 0
+    assert np.allclose(relres2.cpu().numpy(), rel, rtol=1e-3, atol=1e-12)
+    assert np.array_equal(F2.cpu().numpy(), Fg)
 
 
 def test_cg_zero_column_warm_start_and_ragged_c():

@@ -214,6 +214,7 @@ def test_precond_apply_fp32_matches_definition(k, c):
 
 
 @pytest.mark.parametrize("route,dtype,tol", [(hgl.HGL_ROUTE_BR, hgl.HGL_FP32, 1e-8),
+                                             (hgl.HGL_ROUTE_BR, hgl.HGL_FP32, 3e-6),
                                              (hgl.HGL_ROUTE_CG, hgl.HGL_FP64, 1e-10)])
 def test_captured_step_matches_oracle_each_step(route, dtype, tol):
     """HGL_STEP_GRAPH: the first call runs eagerly, the second captures the step into a
@@ -252,6 +253,29 @@ def test_captured_step_matches_oracle_each_step(route, dtype, tol):
     st = hgl.adaptive_step(g, wt, Y, F2, wl.lam, mu, eta, tol=tol, dtype=dtype, route=route, block_ptr=bp,
                            k=16, p=8, q=2, seed=SEED + 9, flags=hgl.HGL_STEP_GRAPH)
     assert st.solve.relres_max <= tol
+
+
+def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs():
+    """With eta = 0 the weights stay put, so from the second step on the warm-started F
+    already meets tol and the captured solve skips its sweeps; at tol = 3e-6 it starts
+    from an FP32 estimate of the residual, and the relres it reports must still be the
+    FP64-accurate one (the host's FP64 residual of the returned F)."""
+    wl, d, H, w, g = _setup(n=5000, m=8000, c=6, seed=14)
+    tol = 3e-6
+    wt = torch.tensor(w, device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    den = np.linalg.norm(wl.lam * d["Y"], axis=0)
+    for i in range(4):
+        w_before = wt.cpu().numpy().copy()
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 0.0, 0.0, tol=tol, dtype=hgl.HGL_FP32,
+                               route=hgl.HGL_ROUTE_BR, block_ptr=d["block_ptr"], k=16, p=8, q=2,
+                               seed=SEED + i, flags=hgl.HGL_STEP_GRAPH)
+        R = wl.lam * d["Y"] - core.theta_apply(H, w_before, F.cpu().numpy(), 1.0 + wl.lam, -1.0)
+        rel = np.linalg.norm(R, axis=0) / den
+        assert rel.max() <= tol and st.solve.relres_max <= tol, (i, rel.max(), st.solve.relres_max)
+        assert np.isclose(st.solve.relres_max, rel.max(), rtol=1e-3, atol=1e-13), (i, rel.max(), st.solve.relres_max)
+    assert np.allclose(wt.cpu().numpy(), w, rtol=1e-12, atol=0)
 
 
 def test_captured_step_rejects_bf16_panels():
