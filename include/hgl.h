@@ -308,6 +308,18 @@ hgl_status hgl_precond_export(const hgl_precond* P, int32_t b, double* Q, double
 hgl_status hgl_precond_apply(const hgl_precond* P, const void* R, int64_t ldr, void* Z,
                              int64_t ldz, int32_t c, hgl_dtype dtype, void* stream);
 
+/*
+ * hgl_precond_tensor_cores -- choose how FP32 panels are applied when the factors are
+ * FP32 (gemm_dtype BF16) and k <= 64: on = 1 (the default) runs the projection and the
+ * expansion of Eq. 15 as TF32 tensor-core products with each operand split into two
+ * TF32 numbers (three products per pair, ~2^-21 relative error per product, FP32
+ * accumulation) and takes the PCG's r.z from the projection; on = 0 runs them on the
+ * FP32 CUDA cores.  Other preconditioners and panel types ignore the switch.  *active
+ * (optional, host) returns whether the tensor-core apply is available for P.
+ * Applies to later calls on P.
+ */
+hgl_status hgl_precond_tensor_cores(hgl_precond* P, int32_t on, int32_t* active);
+
 /* ------------------------------------------------------------------------- */
 /* Weight update (Section 2, Eqs. 4 and 5)                                   */
 /* ------------------------------------------------------------------------- */

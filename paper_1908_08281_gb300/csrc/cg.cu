@@ -11,6 +11,7 @@
 #include <cmath>
 #include <vector>
 
+#include "precond.cuh"
 #include "solver.cuh"
 #include "vec_kernels.cuh"
 
@@ -177,13 +178,15 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
   sm->int_bytes = sizeof(int32_t) * 4 * (size_t)c + 64;
   sm->int_base = iv;
   // partials: two arrays of max(rows) x c
-  const int rows = std::max(op_partial_rows(g), g->num_sms * 4);
+  const int rows = solver_partial_rows(g);
   double* pa = static_cast<double*>(buffer_get(g->partials, sizeof(double) * 2 * (size_t)rows * c, &stt));
   if (!pa) return stt;
   sm->pa = pa;
   sm->pb = pa + (size_t)rows * c;
   return HGL_OK;
 }
+
+int solver_partial_rows(const hgl_graph* g) { return std::max(op_partial_rows(g), g->num_sms * 4); }
 
 // One CG iteration (Eqs. 16-20) on panels of type TP (search direction) / TV (others).
 template <class TP, class TV>
@@ -566,6 +569,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
     extras->state = S;
   }
   HGL_TRY(fill_stats(S, c, sweeps > 0 ? sweeps - 1 : 0, tol, relres_out, iters_out, stats, st, &verdict));
+  if (P) HGL_TRY(precond_tc_status(const_cast<hgl_precond*>(P), st));
   return verdict;
 }
 

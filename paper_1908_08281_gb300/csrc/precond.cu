@@ -486,6 +486,10 @@ hgl_status precond_check(const hgl_precond* P, const hgl_graph* g, double lam) {
 hgl_status precond_reserve(hgl_precond* P, int c, int dt) {
   hgl_status s = HGL_OK;
   const bool f32q = P->dtype == HGL_BF16;
+  if (dt == HGL_FP32 && P->tc) {  // the tensor-core apply's C hi/lo
+    const int64_t c128 = (c + 127) / 128 * 128;
+    if (!buffer_get(P->cbuf, sizeof(float) * 2 * (size_t)P->nb * c128 * P->kp, &s)) return s;
+  }
   if (dt == HGL_FP32 && f32q && P->k <= PF_R && P->k % 4 == 0) {
     const int64_t ldp = (c + 3) / 4 * 4;
     if (!buffer_get(P->pbuf, sizeof(float) * (size_t)P->nslabs * PF_R * ldp, &s)) return s;
@@ -508,7 +512,17 @@ hgl_status precond_apply_launch(const hgl_precond* Pc, const hgl_graph* g, const
     else
       HGL_TRY((apply_typed<double, double>(P, (const double*)R, ldr, (double*)Z, ldz, c, st, run_flag)));
   } else if (dt == HGL_FP32) {
-    if (f32q && P->k <= PF_R && P->k % 4 == 0)
+    if (precond_tc_usable(P, R, ldr, Z, ldz)) {
+      // tensor cores; the projection also gives the per-block r.z partials when the
+      // caller's partial array has room for nb rows
+      const bool rz_here = partials_rz && P->nb <= solver_partial_rows(g);
+      HGL_TRY(precond_tc_apply(P, (const float*)R, ldr, (float*)Z, ldz, c, rz_here ? partials_rz : nullptr, st,
+                               run_flag));
+      if (rz_here) {
+        *rows = P->nb;
+        return HGL_OK;
+      }
+    } else if (f32q && P->k <= PF_R && P->k % 4 == 0)
       HGL_TRY(apply_fast_f32(P, (const float*)R, ldr, (float*)Z, ldz, c, st, run_flag));
     else if (f32q)
       HGL_TRY((apply_typed<float, float>(P, (const float*)R, ldr, (float*)Z, ldz, c, st, run_flag)));

@@ -49,20 +49,30 @@ hgl_status get_encoder(EncodeTiledFn* out) {
   return HGL_OK;
 }
 
-// 2-D BF16 tensor map, 128-byte swizzle, box of 64 elements x box_rows rows.
-hgl_status make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
-                    uint32_t box_rows) {
+}  // namespace
+
+hgl_status encode_map_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                         uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
   EncodeTiledFn enc = nullptr;
   HGL_TRY(get_encoder(&enc));
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {row_bytes};
-  cuuint32_t box[2] = {64u, box_rows};
+  cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1u, 1u};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  // out-of-range elements of a box read as zero (OOB fill NONE fills zeros)
+  CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return record_error(HGL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return HGL_OK;
+}
+
+namespace {
+
+// 2-D BF16 tensor map, 128-byte swizzle, box of 64 elements x box_rows rows.
+hgl_status make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+                    uint32_t box_rows) {
+  return encode_map_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, inner, outer, row_bytes, 64u, box_rows,
+                       CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 #define HGL_LPAD_SWITCH(lp, ...)                              \
@@ -382,6 +392,18 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
   const size_t oBs = take(4 * bs0.size());
   const size_t oEb = take(4 * eb.size());
   const size_t oEt = take(4 * et.size());
+  // tensor-core apply: FP32 factors of rank <= 64, split into TF32 pairs
+  P->tc = bf16 && k <= 64;
+  P->kp = k <= 32 ? 32 : 64;
+  P->n4 = rup(g->n, 4);
+  const size_t tcq = P->tc ? 4 * (size_t)g->n * P->kp : 0;
+  const size_t tcqt = P->tc ? 4 * (size_t)P->kp * P->n4 : 0;
+  const size_t oQh = take(tcq), oQl = take(tcq), oQTh = take(tcqt), oQTl = take(tcqt);
+  const size_t oOrd = take(4 * (size_t)nb);
+  const size_t oErr = take(4);
+  std::vector<int32_t> order(nb);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return wk.rows[a] > wk.rows[b]; });
   cudaError_t e = cudaMalloc(&P->dev, off);
   if (e != cudaSuccess) {
     P->dev = nullptr;
@@ -402,6 +424,14 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
   P->blk_slab0 = reinterpret_cast<int32_t*>(base + oBs);
   P->exp_block = reinterpret_cast<int32_t*>(base + oEb);
   P->exp_tile = reinterpret_cast<int32_t*>(base + oEt);
+  if (P->tc) {
+    P->Qh = reinterpret_cast<float*>(base + oQh);
+    P->Ql = reinterpret_cast<float*>(base + oQl);
+    P->QTh = reinterpret_cast<float*>(base + oQTh);
+    P->QTl = reinterpret_cast<float*>(base + oQTl);
+  }
+  P->blk_order = reinterpret_cast<int32_t*>(base + oOrd);
+  P->d_err = reinterpret_cast<int32_t*>(base + oErr);
   hgl_status fin = HGL_OK;
   auto chk = [&](cudaError_t ce) {
     if (ce != cudaSuccess && fin == HGL_OK) fin = cuda_error(ce, "preconditioner setup", __FILE__, __LINE__);
@@ -416,7 +446,10 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
   chk(cudaMemcpyAsync(P->blk_slab0, bs0.data(), 4 * bs0.size(), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->exp_block, eb.data(), 4 * eb.size(), cudaMemcpyHostToDevice, st));
   chk(cudaMemcpyAsync(P->exp_tile, et.data(), 4 * et.size(), cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(P->blk_order, order.data(), 4 * (size_t)nb, cudaMemcpyHostToDevice, st));
+  chk(cudaMemsetAsync(P->d_err, 0, 4, st));
   chk(cudaStreamSynchronize(st));  // the host vectors above go out of scope
+  if (fin == HGL_OK && P->tc) fin = precond_tc_maps(P);
   if (fin != HGL_OK) {
     precond_plan_destroy(pl);
     return fin;
@@ -520,7 +553,8 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
   });
   HGL_TRY(s_);
   HGL_CHECK_CUDA(cudaGetLastError());
-  return precond_gains_launch(P, wk.ev, lpad, st);
+  HGL_TRY(precond_gains_launch(P, wk.ev, lpad, st));
+  return P->tc ? precond_tc_prepare(P, st) : HGL_OK;
 }
 
 // The device status words of the last compute: HGL_ERR_TIMEOUT if the tensor-core
@@ -530,7 +564,7 @@ hgl_status precond_plan_check(PrecondPlan* pl, cudaStream_t st) {
   HGL_CHECK_CUDA(cudaMemcpyAsync(flags, pl->wk.fail, 8, cudaMemcpyDeviceToHost, st));
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   if (flags[1] != 0) return record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
-  return HGL_OK;
+  return precond_tc_status(pl->P, st);
 }
 
 const hgl_precond* precond_plan_handle(const PrecondPlan* pl) { return pl->P; }

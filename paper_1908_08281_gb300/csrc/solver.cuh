@@ -105,6 +105,9 @@ hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, 
 // Preconditioner hooks (rsvd.cu).  Z = P^-1 R on panels of `dt` (FP64 or FP32) and,
 // when partials_rz is given, per-column partial sums of R.Z (row count in *rows).
 hgl_status precond_check(const hgl_precond* P, const hgl_graph* g, double lam);
+// Rows of each of the solver's two FP64 partial-sum arrays (row stride c).
+int solver_partial_rows(const hgl_graph* g);
+
 hgl_status precond_apply_launch(const hgl_precond* P, const hgl_graph* g, const void* R, int64_t ldr, void* Z,
                                 int64_t ldz, int c, int dt, double* partials_rz, cudaStream_t st, int* rows,
                                 const int32_t* run_flag);

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "hgl_precond_destroy": (None, [_P]),
     "hgl_precond_export": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(_I32), _P]),
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
+    "hgl_precond_tensor_cores": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
@@ -369,6 +370,14 @@ def precond_apply(P: Precond, R: torch.Tensor, Z: torch.Tensor | None = None, st
     pz, ldz, _ = _panel(Z, "Z")
     _check(lib().hgl_precond_apply(P.handle, pr, ldr, pz, ldz, c, dt, _stream(stream)))
     return Z
+
+
+def precond_tensor_cores(P: Precond, on: bool) -> bool:
+    """Select the TF32 tensor-core apply (split operands, FP32 accuracy) or the FP32
+    CUDA-core apply for FP32 panels; returns whether P supports the tensor-core one."""
+    active = ctypes.c_int32(0)
+    _check(lib().hgl_precond_tensor_cores(P.handle, 1 if on else 0, ctypes.byref(active)))
+    return bool(active.value)
 
 
 def weight_grad(g: Graph, w: torch.Tensor, F: torch.Tensor, mu: float = 0.0, Z: torch.Tensor | None = None,

@@ -104,6 +104,28 @@ def test_rsvd_bf16_tensor_cores_vs_fp64(k, p):
         assert np.linalg.norm(Z - Z64) <= 3e-2 * np.linalg.norm(Z64)
 
 
+def test_pcg_fp32_tensor_core_apply_matches_cuda_core_apply():
+    """The FP32 PCG with the tensor-core apply (whose projection also gives r.z) against
+    the same solve with the CUDA-core apply: both converge, with iteration counts within
+    one of each other, to the same solution within the tolerance's error bound."""
+    wl, d, H, w, g = _setup(n=9000, m=15000, c=40, seed=8)
+    bp = d["block_ptr"]
+    wt = torch.tensor(w, device=DEV)
+    Pc = hgl.block_rsvd(g, wt, wl.lam, bp, 64, 10, 2, SEED, gemm_dtype=hgl.HGL_BF16)
+    Y = _panel(d["Y"])
+    out = {}
+    for tc in (True, False):
+        assert hgl.precond_tensor_cores(Pc, tc)
+        F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=1e-8, dtype=hgl.HGL_FP32, precond=Pc)
+        assert st.relres_max <= 1e-8
+        out[tc] = (F.cpu().numpy(), iters.cpu().numpy())
+    assert np.abs(out[True][1].astype(int) - out[False][1].astype(int)).max() <= 1
+    ref, _ = core.certified_solve(H, w, wl.lam, d["Y"])
+    for tc in (True, False):
+        err = np.linalg.norm(out[tc][0] - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert err.max() <= (1 + wl.lam) / wl.lam * 1e-8 * 1.01, (tc, err.max())
+
+
 def test_pcg_fp64_reaches_oracle_solution():
     wl, d, H, w, g = _setup(n=2000, m=3000, c=6, seed=5)
     bp = d["block_ptr"]
@@ -184,17 +206,21 @@ def test_br_loop_through_weight_collapse_mixed_precision():
     assert torch.topk(wt, 10).values.sum().item() > 0.9
 
 
+@pytest.mark.parametrize("tc", [True, False])
 @pytest.mark.parametrize("k", [64, 20, 18])
 @pytest.mark.parametrize("c", [5, 130, 300])
-def test_precond_apply_fp32_matches_definition(k, c):
+def test_precond_apply_fp32_matches_definition(k, c, tc):
     """Z = R/(1+lam) + sum_b Q_b diag(g_b) Q_b^T R_b (Eq. 15 with the Woodbury gains),
-    evaluated in FP64 from the exported factors, against the FP32 apply: blocks larger
-    than one projection slab (2048 rows), ragged tiles, ragged column chunks; k = 64 and
-    k = 20 take the register-tiled kernels, k = 18 the generic ones."""
+    evaluated in FP64 from the exported factors, against the FP32 apply: blocks that
+    start off every 32-row boundary and span several tiles, ragged tiles, ragged column
+    chunks.  tc: the TF32 tensor-core apply with split operands (rank padded to 32 or
+    64); else k = 64 and k = 20 take the register-tiled CUDA-core kernels, k = 18 the
+    generic ones."""
     wl, d, H, w, g = _setup(n=20000, m=33000, seed=5)
     bp = [0, 5000, 8000, 8130, 10179, 14275, 20000]
     lam = wl.lam
     Pc = hgl.block_rsvd(g, torch.tensor(w, device=DEV), lam, bp, k, 8, 1, SEED, gemm_dtype=hgl.HGL_BF16)
+    assert hgl.precond_tensor_cores(Pc, tc)
     rng = np.random.default_rng(k + c)
     R32 = _panel(rng.standard_normal((d["n"], c)), torch.float32)
     R = R32.to(torch.float64).cpu().numpy()
