@@ -37,12 +37,10 @@ using umma::tf32_round;
 using umma::tma_load_2d;
 
 constexpr int TC_THREADS = 256;
-constexpr int PJ_STAGES = 3;
 constexpr int PJ_ROWS = 32;   // block rows per projection step (one 128-byte TF32 K slice)
 constexpr int PJ_COLS = 128;  // panel columns per projection unit (the MMA's M)
 constexpr int EX_ROWS = 128;  // rows per expansion unit (the MMA's M)
 constexpr int EX_COLS = 64;   // panel columns per expansion step (the MMA's N)
-constexpr int EX_STAGES = 2;
 
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -86,11 +84,15 @@ k_tc_split(int64_t n, int64_t n4, int k, const float* __restrict__ Q, float* __r
 // ---------------------------------------------------------------------------
 // Projection.  Work unit = (block b, 128-column tile); units run in decreasing block
 // size over persistent CTAs.  Per step of 32 block rows:
-//   warp 0 (one lane): TMA of the R rows (32 x 128 FP32, unswizzled staging) and of
-//          Q_b^T hi/lo (KP x 32, K-major, 128-byte swizzle) into a ring stage;
+//   warp 0 (one lane): TMA of the R rows (32 x 128 FP32, unswizzled) into a deep ring
+//          of R stages (the DRAM stream: enough bytes in flight to cover its latency);
+//   warp 3 (one lane): TMA of Q_b^T hi/lo (KP x 32, K-major, 128-byte swizzle) into a
+//          ring of operand stages;
 //   warps 4-7 (thread t = panel column j): read column j of the staged rows, zero the
-//          rows outside the block, accumulate r.r, split into TF32 hi/lo and write them
-//          transposed (row t of a K-major 128 x 32 tile, 128-byte swizzle);
+//          rows outside the block, accumulate r.r, split into TF32 hi + lo and write
+//          them transposed (row t of a K-major 128 x 32 tile, 128-byte swizzle) into
+//          the operand stage (lo is left for the MMA to truncate to TF32: its error,
+//          2^-10 of lo, is 2^-21 of the element);
 //   warp 1 (one lane): 4 K-substeps x 3 MMAs  D[j, i] += A[j, :] B[i, :]  (D = C^T, M =
 //          128 columns, N = KP ranks, accumulated in TMEM over the whole block).
 // Epilogue (warps 4-7, lane = column j): C[:, j] from TMEM, c_i = g_i C_ij split into
@@ -110,9 +112,42 @@ struct PjArgs {
   int* err;
 };
 
+constexpr int PJ_RSTAGES = 6;   // R stages (16 KB each)
+constexpr int PJ_ABSTAGES = 2;  // operand stages (A hi/lo + B hi/lo)
+constexpr uint32_t PJ_R_BYTES = PJ_ROWS * PJ_COLS * 4;
+constexpr uint32_t PJ_A_BYTES = PJ_COLS * 128;
+
 template <int KP>
-__host__ __device__ constexpr uint32_t pj_stage_bytes() {
-  return PJ_ROWS * PJ_COLS * 4 + 2 * PJ_COLS * 128 + 2 * KP * 128;
+__host__ __device__ constexpr uint32_t pj_ab_bytes() {
+  return 2 * PJ_A_BYTES + 2 * KP * 128;
+}
+template <int KP>
+__host__ __device__ constexpr uint32_t pj_smem_bytes() {
+  return 1024 + PJ_RSTAGES * PJ_R_BYTES + PJ_ABSTAGES * pj_ab_bytes<KP>() + 256;
+}
+
+// One 32-row step of the builders: column t of the staged rows, rows [lo, hi) kept.
+template <bool MASK>
+__device__ __forceinline__ float pj_build(const float* __restrict__ stg, uint8_t* ah, uint8_t* al, int t, int lo,
+                                          int hi) {
+  float ss = 0.f;
+#pragma unroll
+  for (int g = 0; g < PJ_ROWS / 4; ++g) {
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = 4 * g + e;
+      float x = stg[i * PJ_COLS + t];
+      if (MASK && (i < lo || i >= hi)) x = 0.f;  // rows of the neighbouring blocks
+      ss = fmaf(x, x, ss);
+      h[e] = tf32_round(x);
+      l[e] = x - h[e];
+    }
+    const uint32_t off = sw128_offset_f32(t, 4 * g);
+    *reinterpret_cast<float4*>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4*>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+  return ss;
 }
 
 template <int KP>
@@ -120,23 +155,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapQTh,
              const __grid_constant__ CUtensorMap mapQTl, PjArgs a) {
   if (a.run_flag && *a.run_flag == 0) return;
-  constexpr uint32_t R_BYTES = PJ_ROWS * PJ_COLS * 4;  // 16 KB staging
-  constexpr uint32_t A_BYTES = PJ_COLS * 128;          // 16 KB per split
-  constexpr uint32_t B_BYTES = KP * 128;               // per split
-  constexpr uint32_t STAGE = pj_stage_bytes<KP>();
-  constexpr uint32_t TX_BYTES = R_BYTES + 2 * B_BYTES;
+  constexpr uint32_t B_BYTES = KP * 128;  // per split
+  constexpr uint32_t AB = pj_ab_bytes<KP>();
   constexpr uint32_t ACC_COLS = KP;
   constexpr uint32_t TMEM_COLS = 2 * KP;
   constexpr uint32_t IDESC = umma::idesc_tf32_f32(PJ_COLS, KP);
-  static_assert(STAGE % 1024 == 0, "stages must keep 1024-byte alignment");
+  static_assert(PJ_R_BYTES % 1024 == 0 && AB % 1024 == 0, "stages must keep 1024-byte alignment");
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* tma_full = reinterpret_cast<uint64_t*>(smem + PJ_STAGES * STAGE);
-  uint64_t* a_full = tma_full + PJ_STAGES;
-  uint64_t* empty = a_full + PJ_STAGES;
-  uint64_t* acc_full = empty + PJ_STAGES;  // 2
-  uint64_t* acc_empty = acc_full + 2;      // 2
+  uint8_t* sR = smem;
+  uint8_t* sAB = smem + PJ_RSTAGES * PJ_R_BYTES;
+  uint64_t* r_full = reinterpret_cast<uint64_t*>(sAB + PJ_ABSTAGES * AB);
+  uint64_t* r_empty = r_full + PJ_RSTAGES;
+  uint64_t* b_full = r_empty + PJ_RSTAGES;
+  uint64_t* a_full = b_full + PJ_ABSTAGES;
+  uint64_t* ab_empty = a_full + PJ_ABSTAGES;
+  uint64_t* acc_full = ab_empty + PJ_ABSTAGES;  // 2
+  uint64_t* acc_empty = acc_full + 2;           // 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5;
@@ -144,10 +180,14 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
   const int nunits = a.nb * a.nct;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PJ_STAGES; ++s) {
-      mbar_init(tma_full + s, 1);
-      mbar_init(a_full + s, 4);  // one arrival per builder warp
-      mbar_init(empty + s, 1);
+    for (int s = 0; s < PJ_RSTAGES; ++s) {
+      mbar_init(r_full + s, 1);
+      mbar_init(r_empty + s, 4);  // one arrival per builder warp
+    }
+    for (int s = 0; s < PJ_ABSTAGES; ++s) {
+      mbar_init(b_full + s, 1);
+      mbar_init(a_full + s, 4);
+      mbar_init(ab_empty + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
@@ -170,9 +210,13 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
     nsteps = (int)((bend - rs + PJ_ROWS - 1) / PJ_ROWS);
   };
 
-  if (warp == 0) {
-    // ---------------- TMA producer ----------------
+  if (warp == 0 || warp == 3) {
+    // ---------------- TMA producers: R (warp 0), Q^T hi/lo (warp 3) ----------------
     if (lane == 0) {
+      const bool rprod = warp == 0;
+      const int nst = rprod ? PJ_RSTAGES : PJ_ABSTAGES;
+      uint64_t* full = rprod ? r_full : b_full;
+      uint64_t* empty = rprod ? r_empty : ab_empty;
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -185,13 +229,17 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
             ok = false;
             break;
           }
-          uint8_t* sb = smem + stage * STAGE;
           const int row = (int)(rs + (int64_t)s * PJ_ROWS);
-          mbar_arrive_expect_tx(tma_full + stage, TX_BYTES);
-          tma_load_2d(sb, &mapR, tma_full + stage, ct * PJ_COLS, row);
-          tma_load_2d(sb + R_BYTES + 2 * A_BYTES, &mapQTh, tma_full + stage, row, 0);
-          tma_load_2d(sb + R_BYTES + 2 * A_BYTES + B_BYTES, &mapQTl, tma_full + stage, row, 0);
-          if (++stage == PJ_STAGES) {
+          if (rprod) {
+            mbar_arrive_expect_tx(full + stage, PJ_R_BYTES);
+            tma_load_2d(sR + stage * PJ_R_BYTES, &mapR, full + stage, ct * PJ_COLS, row);
+          } else {
+            uint8_t* sb = sAB + stage * AB + 2 * PJ_A_BYTES;
+            mbar_arrive_expect_tx(full + stage, 2 * B_BYTES);
+            tma_load_2d(sb, &mapQTh, full + stage, row, 0);
+            tma_load_2d(sb + B_BYTES, &mapQTl, full + stage, row, 0);
+          }
+          if (++stage == nst) {
             stage = 0;
             phase ^= 1;
           }
@@ -214,14 +262,15 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)acc * ACC_COLS;
         for (int s = 0; s < nsteps; ++s) {
-          if (!mbar_wait(tma_full + stage, phase, a.err) || !mbar_wait(a_full + stage, phase, a.err)) {
+          if (!mbar_wait(b_full + stage, phase, a.err) || !mbar_wait(a_full + stage, phase, a.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(smem + stage * STAGE + R_BYTES);
-          const uint64_t ah = smem_desc_sw128(sa), al = smem_desc_sw128(sa + A_BYTES);
-          const uint64_t bh = smem_desc_sw128(sa + 2 * A_BYTES), bl = smem_desc_sw128(sa + 2 * A_BYTES + B_BYTES);
+          const uint32_t sa = smem_u32(sAB + stage * AB);
+          const uint64_t ah = smem_desc_sw128(sa), al = smem_desc_sw128(sa + PJ_A_BYTES);
+          const uint64_t bh = smem_desc_sw128(sa + 2 * PJ_A_BYTES);
+          const uint64_t bl = smem_desc_sw128(sa + 2 * PJ_A_BYTES + B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < PJ_ROWS / 8; ++kk) {
             // 8 TF32 elements (32 bytes) along K per MMA inside the 128-byte swizzled row
@@ -230,8 +279,8 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
             umma::mma_tf32(d_tmem, ah + off, bl + off, IDESC, 1u);
             umma::mma_tf32(d_tmem, al + off, bh + off, IDESC, 1u);
           }
-          umma::mma_commit(empty + stage);
-          if (++stage == PJ_STAGES) {
+          umma::mma_commit(ab_empty + stage);
+          if (++stage == PJ_ABSTAGES) {
             stage = 0;
             phase ^= 1;
           }
@@ -248,8 +297,8 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
     // ---------------- operand builders, then the epilogue ----------------
     const int quarter = warp & 3;
     const int t = quarter * 32 + lane;  // A row = panel column of the unit
-    int stage = 0;
-    uint32_t phase = 0;
+    int rstage = 0, astage = 0;
+    uint32_t rphase = 0, aphase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
@@ -257,40 +306,34 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       int b, ct, nsteps;
       int64_t b0, bend, rs;
       unit_rows(u, b, ct, b0, bend, rs, nsteps);
-      DotAcc<float> rr;
+      double rr = 0.0;
       for (int s = 0; s < nsteps; ++s) {
-        if (!mbar_wait(tma_full + stage, phase, a.err)) {
+        if (!mbar_wait(r_full + rstage, rphase, a.err) || !mbar_wait(ab_empty + astage, aphase ^ 1, a.err)) {
           ok = false;
           break;
         }
-        uint8_t* sb = smem + stage * STAGE;
-        const float* stg = reinterpret_cast<const float*>(sb);
-        uint8_t* ah = sb + R_BYTES;
-        uint8_t* al = ah + A_BYTES;
+        const float* stg = reinterpret_cast<const float*>(sR + rstage * PJ_R_BYTES);
+        uint8_t* ah = sAB + astage * AB;
         const int64_t row0 = rs + (int64_t)s * PJ_ROWS;
-#pragma unroll
-        for (int g = 0; g < PJ_ROWS / 4; ++g) {
-          float h[4], l[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int i = 4 * g + e;
-            const int64_t row = row0 + i;
-            float x = stg[i * PJ_COLS + t];
-            if (row < b0 || row >= bend) x = 0.f;  // rows of the neighbouring blocks
-            rr.add(x, x);
-            h[e] = tf32_round(x);
-            l[e] = tf32_round(x - h[e]);
-          }
-          const uint32_t off = sw128_offset_f32(t, 4 * g);
-          *reinterpret_cast<float4*>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<float4*>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
-        }
+        const int lo = (int)(b0 > row0 ? b0 - row0 : 0);
+        const int hi = (int)(bend - row0 < PJ_ROWS ? bend - row0 : PJ_ROWS);
+        // r.r per 32-row step in FP32, across steps in FP64
+        const float ss = (lo == 0 && hi == PJ_ROWS) ? pj_build<false>(stg, ah, ah + PJ_A_BYTES, t, 0, PJ_ROWS)
+                                                    : pj_build<true>(stg, ah, ah + PJ_A_BYTES, t, lo, hi);
+        rr += (double)ss;
         umma::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(a_full + stage);
-        if (++stage == PJ_STAGES) {
-          stage = 0;
-          phase ^= 1;
+        if (lane == 0) {
+          mbar_arrive(r_empty + rstage);
+          mbar_arrive(a_full + astage);
+        }
+        if (++rstage == PJ_RSTAGES) {
+          rstage = 0;
+          rphase ^= 1;
+        }
+        if (++astage == PJ_ABSTAGES) {
+          astage = 0;
+          aphase ^= 1;
         }
       }
       if (!ok) break;
@@ -315,7 +358,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       }
       const int j = ct * PJ_COLS + t;
       const double* gb = a.gain + (int64_t)b * a.k;
-      double rz = rr.value() * a.inv1l;
+      double rz = rr * a.inv1l;
       float* ch = a.Ch + ((int64_t)b * a.c128 + j) * KP;
       float* cl = a.Cl + ((int64_t)b * a.c128 + j) * KP;
 #pragma unroll
@@ -344,13 +387,14 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
   }
 }
 
-
 // ---------------------------------------------------------------------------
 // Expansion.  Work unit = one 128-row tile of a block (rows past the block's end are
 // computed from the next block's factors and discarded); per unit the Q_b rows (hi/lo,
-// 128 x KP) stay in shared memory while the column steps of 64 stream through a ring:
+// 128 x KP) stay in shared memory while the column steps of 64 stream through:
 //   warp 0 (one lane): TMA of Q rows once per unit, then per step the C_b^T rows hi/lo
-//          (64 x KP) and the R tile (128 x 64, two 128-byte-swizzled boxes);
+//          (64 x KP) into a ring of operand stages;
+//   warp 3 (one lane): TMA of the R tile (128 x 64, two 128-byte-swizzled boxes) into a
+//          deeper ring of R stages (the DRAM stream);
 //   warp 1 (one lane): KP/8 K-substeps x 3 MMAs  D[r, j] += Q[r, :] C[:, j];
 //   warps 4-7 (lane = row): z = R/(1+lam) + D written over the staged R, then stored to
 //          Z by whole rows (two rows of 64 columns per warp instruction).
@@ -369,13 +413,22 @@ struct ExArgs {
   int* err;
 };
 
+constexpr int EX_RSTAGES = 3;
+constexpr int EX_BSTAGES = 2;
+constexpr uint32_t EX_RBOX = EX_ROWS * 128;                  // 16 KB (32 columns)
+constexpr uint32_t EX_R_BYTES = (EX_COLS / 32) * EX_RBOX;    // 32 KB per R stage
+
 template <int KP>
 __host__ __device__ constexpr uint32_t ex_a_bytes() {
   return 2 * (KP / 32) * EX_ROWS * 128;
 }
 template <int KP>
-__host__ __device__ constexpr uint32_t ex_stage_bytes() {
-  return 2 * (KP / 32) * EX_COLS * 128 + (EX_COLS / 32) * EX_ROWS * 128;
+__host__ __device__ constexpr uint32_t ex_b_bytes() {
+  return 2 * (KP / 32) * EX_COLS * 128;
+}
+template <int KP>
+__host__ __device__ constexpr uint32_t ex_smem_bytes() {
+  return 1024 + ex_a_bytes<KP>() + EX_BSTAGES * ex_b_bytes<KP>() + EX_RSTAGES * EX_R_BYTES + 256;
 }
 
 template <int KP>
@@ -384,28 +437,29 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
                const __grid_constant__ CUtensorMap mapQl, const __grid_constant__ CUtensorMap mapCh,
                const __grid_constant__ CUtensorMap mapCl, ExArgs a) {
   if (a.run_flag && *a.run_flag == 0) return;
-  constexpr int KB = KP / 32;                            // 128-byte K boxes
-  constexpr uint32_t QBOX = EX_ROWS * 128;               // 16 KB
-  constexpr uint32_t A_BYTES = ex_a_bytes<KP>();         // Qh then Ql
-  constexpr uint32_t CBOX = EX_COLS * 128;               // 8 KB
-  constexpr uint32_t B_BYTES = 2 * KB * CBOX;            // Ch then Cl
-  constexpr uint32_t RBOX = EX_ROWS * 128;               // 16 KB (32 columns)
-  constexpr uint32_t STAGE = ex_stage_bytes<KP>();       // B then the R boxes
+  constexpr int KB = KP / 32;                     // 128-byte K boxes
+  constexpr uint32_t QBOX = EX_ROWS * 128;        // 16 KB
+  constexpr uint32_t A_BYTES = ex_a_bytes<KP>();  // Qh then Ql
+  constexpr uint32_t CBOX = EX_COLS * 128;        // 8 KB
+  constexpr uint32_t B_BYTES = ex_b_bytes<KP>();  // Ch then Cl
   constexpr uint32_t ACC_COLS = EX_COLS;
   constexpr uint32_t TMEM_COLS = 2 * EX_COLS;
   constexpr uint32_t IDESC = umma::idesc_tf32_f32(EX_ROWS, EX_COLS);
-  static_assert(A_BYTES % 1024 == 0 && STAGE % 1024 == 0, "tiles must keep 1024-byte alignment");
+  static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "tiles must keep 1024-byte alignment");
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
-  uint8_t* sStages = smem + A_BYTES;
-  uint64_t* a_full = reinterpret_cast<uint64_t*>(sStages + EX_STAGES * STAGE);
+  uint8_t* sB = smem + A_BYTES;
+  uint8_t* sR = sB + EX_BSTAGES * B_BYTES;
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(sR + EX_RSTAGES * EX_R_BYTES);
   uint64_t* a_empty = a_full + 1;
-  uint64_t* full = a_empty + 1;
-  uint64_t* empty = full + EX_STAGES;
-  uint64_t* acc_full = empty + EX_STAGES;  // 2
-  uint64_t* acc_empty = acc_full + 2;      // 2
+  uint64_t* b_full = a_empty + 1;
+  uint64_t* b_empty = b_full + EX_BSTAGES;
+  uint64_t* r_full = b_empty + EX_BSTAGES;
+  uint64_t* r_empty = r_full + EX_RSTAGES;
+  uint64_t* acc_full = r_empty + EX_RSTAGES;  // 2
+  uint64_t* acc_empty = acc_full + 2;         // 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
   const int warp = threadIdx.x >> 5;
@@ -414,9 +468,13 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
     mbar_init(a_empty, 1);
-    for (int s = 0; s < EX_STAGES; ++s) {
-      mbar_init(full + s, 1);
-      mbar_init(empty + s, 5);  // the MMA's commit and one arrival per epilogue warp
+    for (int s = 0; s < EX_BSTAGES; ++s) {
+      mbar_init(b_full + s, 1);
+      mbar_init(b_empty + s, 1);
+    }
+    for (int s = 0; s < EX_RSTAGES; ++s) {
+      mbar_init(r_full + s, 1);
+      mbar_init(r_empty + s, 4);  // one arrival per epilogue warp
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
@@ -431,7 +489,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
-    // ---------------- TMA producer ----------------
+    // ---------------- TMA producer: Q rows and C^T rows ----------------
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0, aphase = 0;
@@ -449,21 +507,44 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
         }
         const int crow = (int)((int64_t)b * a.c128);
         for (int cs = 0; cs < a.ncs; ++cs) {
-          if (!mbar_wait(empty + stage, phase ^ 1, a.err)) {
+          if (!mbar_wait(b_empty + stage, phase ^ 1, a.err)) {
             ok = false;
             break;
           }
-          uint8_t* sb = sStages + stage * STAGE;
-          mbar_arrive_expect_tx(full + stage, STAGE);
+          uint8_t* sb = sB + stage * B_BYTES;
+          mbar_arrive_expect_tx(b_full + stage, B_BYTES);
 #pragma unroll
           for (int q = 0; q < KB; ++q) {
-            tma_load_2d(sb + q * CBOX, &mapCh, full + stage, 32 * q, crow + cs * EX_COLS);
-            tma_load_2d(sb + (KB + q) * CBOX, &mapCl, full + stage, 32 * q, crow + cs * EX_COLS);
+            tma_load_2d(sb + q * CBOX, &mapCh, b_full + stage, 32 * q, crow + cs * EX_COLS);
+            tma_load_2d(sb + (KB + q) * CBOX, &mapCl, b_full + stage, 32 * q, crow + cs * EX_COLS);
           }
+          if (++stage == EX_BSTAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+    }
+  } else if (warp == 3) {
+    // ---------------- TMA producer: R tiles ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < a.nexp && ok; u += gridDim.x) {
+        const int b = a.exp_block[u];
+        const int row0 = (int)(a.v0[b] + (int64_t)a.exp_tile[u] * EX_ROWS);
+        for (int cs = 0; cs < a.ncs; ++cs) {
+          if (!mbar_wait(r_empty + stage, phase ^ 1, a.err)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sr = sR + stage * EX_R_BYTES;
+          mbar_arrive_expect_tx(r_full + stage, EX_R_BYTES);
 #pragma unroll
           for (int h = 0; h < EX_COLS / 32; ++h)
-            tma_load_2d(sb + B_BYTES + h * RBOX, &mapR, full + stage, cs * EX_COLS + 32 * h, row0);
-          if (++stage == EX_STAGES) {
+            tma_load_2d(sr + h * EX_RBOX, &mapR, r_full + stage, cs * EX_COLS + 32 * h, row0);
+          if (++stage == EX_RSTAGES) {
             stage = 0;
             phase ^= 1;
           }
@@ -483,13 +564,13 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
         if (!mbar_wait(a_full, aphase, a.err)) break;
         aphase ^= 1;
         for (int cs = 0; cs < a.ncs; ++cs) {
-          if (!mbar_wait(full + stage, phase, a.err) || !mbar_wait(acc_empty + acc, acc_phase ^ 1, a.err)) {
+          if (!mbar_wait(b_full + stage, phase, a.err) || !mbar_wait(acc_empty + acc, acc_phase ^ 1, a.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)acc * ACC_COLS;
-          const uint32_t b0 = smem_u32(sStages + stage * STAGE);
+          const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < KP / 8; ++kk) {
             const int q = kk >> 2;
@@ -502,9 +583,9 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
             umma::mma_tf32(d_tmem, ah, bl, IDESC, 1u);
             umma::mma_tf32(d_tmem, al, bh, IDESC, 1u);
           }
-          umma::mma_commit(empty + stage);
+          umma::mma_commit(b_empty + stage);
           umma::mma_commit(acc_full + acc);
-          if (++stage == EX_STAGES) {
+          if (++stage == EX_BSTAGES) {
             stage = 0;
             phase ^= 1;
           }
@@ -530,7 +611,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
       const int64_t row0 = a.v0[b] + (int64_t)a.exp_tile[u] * EX_ROWS;
       const int64_t bend = a.v0[b] + a.rows[b];
       for (int cs = 0; cs < a.ncs; ++cs) {
-        if (!mbar_wait(acc_full + acc, acc_phase, a.err) || !mbar_wait(full + stage, phase, a.err)) {
+        if (!mbar_wait(acc_full + acc, acc_phase, a.err) || !mbar_wait(r_full + stage, phase, a.err)) {
           ok = false;
           break;
         }
@@ -553,12 +634,12 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
           acc_phase ^= 1;
         }
         // z = R/(1+lam) + D over this thread's row of the staged R tile
-        uint8_t* rst = sStages + stage * STAGE + B_BYTES;
+        uint8_t* rst = sR + stage * EX_R_BYTES;
 #pragma unroll
         for (int h = 0; h < EX_COLS / 32; ++h)
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
-            float4* p = reinterpret_cast<float4*>(rst + h * RBOX + sw128_offset_f32(t, 4 * g));
+            float4* p = reinterpret_cast<float4*>(rst + h * EX_RBOX + sw128_offset_f32(t, 4 * g));
             const float4 r = *p;
             const int j = 32 * h + 4 * g;
             *p = make_float4(fmaf(a.inv1l, r.x, d[j]), fmaf(a.inv1l, r.y, d[j + 1]), fmaf(a.inv1l, r.z, d[j + 2]),
@@ -573,7 +654,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
           const int rr = quarter * 32 + 2 * it + (lane >> 4);
           const int64_t grow = row0 + rr;
           if (grow >= bend) continue;
-          const float4 z = *reinterpret_cast<const float4*>(rst + h * RBOX + sw128_offset_f32(rr, 4 * g));
+          const float4 z = *reinterpret_cast<const float4*>(rst + h * EX_RBOX + sw128_offset_f32(rr, 4 * g));
           float* zp = a.Z + grow * a.ldz + col;
           if (col + 3 < a.c) {
             *reinterpret_cast<float4*>(zp) = z;
@@ -587,8 +668,8 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
         // before the TMA that refills the stage
         umma::fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty + stage);
-        if (++stage == EX_STAGES) {
+        if (lane == 0) mbar_arrive(r_empty + stage);
+        if (++stage == EX_RSTAGES) {
           stage = 0;
           phase ^= 1;
         }
@@ -640,8 +721,8 @@ hgl_status tc_apply(hgl_precond* P, const float* R, int64_t ldr, float* Z, int64
                         CU_TENSOR_MAP_SWIZZLE_128B));
   HGL_TRY(encode_map_2d(&mCh, f32, Ch, KP, (uint64_t)P->nb * c128, KP * 4, 32, EX_COLS, CU_TENSOR_MAP_SWIZZLE_128B));
   HGL_TRY(encode_map_2d(&mCl, f32, Cl, KP, (uint64_t)P->nb * c128, KP * 4, 32, EX_COLS, CU_TENSOR_MAP_SWIZZLE_128B));
-  const size_t smem_pj = 1024 + PJ_STAGES * (size_t)pj_stage_bytes<KP>() + 256;
-  const size_t smem_ex = 1024 + ex_a_bytes<KP>() + EX_STAGES * (size_t)ex_stage_bytes<KP>() + 256;
+  const size_t smem_pj = pj_smem_bytes<KP>();
+  const size_t smem_ex = ex_smem_bytes<KP>();
   static bool attr_set = false;
   if (!attr_set) {
     HGL_TRY(tc_smem_attr(k_pc_proj_tc<KP>, smem_pj));
