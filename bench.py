@@ -289,7 +289,9 @@ def config_dict(d, bp):
             "lam": wl.lam, "mu": wl.mu, "eta": d.get("eta", wl.eta), "outer_loop": LOOP, "tol_relres": TOL,
             "size_law": synth.describe_sizes(wl), "route": "block rSVD preconditioned CG (BR)",
             "blocks": int(len(bp) - 1), "block_sizes": "U{1024..8192}", "k": K_RANK, "p": P_OVER, "q": Q_ITERS,
-            "panel_dtype": "fp32 (fp64-accurate refinement)", "gemm_dtype": "bf16 tcgen05, fp32 accumulate",
+            "panel_dtype": "fp32 (fp64-accurate refinement)",
+            "block_products": "auto by block fill: fp32 from the incidence lists, or bf16 dense blocks on tcgen05",
+            "precond_apply": "tcgen05 tf32, operands split hi+lo (3 products), fp32 accumulate",
             "l2_flush": "inputs larger than L2 (>= 2 GB panels)"}
 
 
@@ -515,6 +517,8 @@ def main():
             "accuracy": accuracy,
             "roofline": roofline,
             "kernel_families": families,
+            "block_product_route": ("sparse (incidence lists)" if prof[hgl.PROF_BLOCKSPMM][1] > 0
+                                    else "dense (tcgen05 GEMM)"),
             "e2e": e2e,
             "fp64_block_cg": fp64,
             "cpu_baseline": cpu,

@@ -90,7 +90,8 @@ uint64_t hgl_launch_count(void);
 #define HGL_PROF_OPRESID  8   /* residual from one operator pass with the residual      */
                               /* epilogue (FP32 estimate of the mixed solvers, FP64     */
                               /* residual of the FP64 solver)                           */
-#define HGL_PROF_FAMILIES 9
+#define HGL_PROF_BLOCKSPMM 9  /* block rSVD products Theta_bb S on the sparse route    */
+#define HGL_PROF_FAMILIES 10
 hgl_status hgl_profile_enable(int32_t on);
 hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches);
 
@@ -276,9 +277,10 @@ hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double lam, const d
  *   block_ptr  HOST int64[nblocks+1], 0 = block_ptr[0] < ... < block_ptr[nblocks] = n
  *   k, p, q    rank, oversampling, iterations (k >= 1, p >= 0, q >= 0)
  *   seed       seed of the Philox4x32-10 Gaussian test matrix Omega (see below)
- *   gemm_dtype HGL_BF16: Theta_bb and the bases in BF16, products on the tcgen05
- *              tensor cores with FP32 accumulation; HGL_FP64: all products in FP64
- *              on the CUDA cores (slow; for checking)
+ *   gemm_dtype HGL_BF16: products Theta_bb S with FP32 accumulation, by the route of
+ *              hgl_set_block_product (dense BF16 blocks on the tcgen05 tensor cores,
+ *              or FP32 straight from the incidence lists); HGL_FP64: dense FP64
+ *              blocks, all products in FP64 on the CUDA cores (slow; for checking)
  * Omega[g, j] for global vertex row g and column j: x = Philox4x32-10(counter
  * (g, j>>1, 0x4F6D6567, 0), key (seed & 0xffffffff, seed >> 32)); u1, u2 in (0,1) from
  * (x0,x1) and (x2,x3) as ((hi>>5)*2^26 + (lo>>6) + 1/2) * 2^-53; Omega = sqrt(-2 ln u1)
@@ -289,6 +291,26 @@ hgl_status hgl_block_rsvd(const hgl_graph* g, const double* w, double lam,
                           const int64_t* block_ptr, int32_t nblocks, int32_t k, int32_t p,
                           int32_t q, uint64_t seed, hgl_dtype gemm_dtype, void* stream,
                           hgl_precond** out);
+
+/*
+ * hgl_set_block_product -- route of the BF16 path's products Theta_bb S for
+ * preconditioners built on g afterwards (including the captured steps' own):
+ *   HGL_BLOCKS_DENSE   assemble the diagonal blocks as dense BF16 matrices and multiply
+ *                      them on the tcgen05 tensor cores (grouped GEMM): cost set by the
+ *                      sum of the squared block sizes;
+ *   HGL_BLOCKS_SPARSE  no dense blocks: each vertex row of Theta_bb S is summed from
+ *                      its hyperedges' members inside its block (found by binary search
+ *                      in the sorted member lists), FP32 basis and accumulation: cost
+ *                      set by the blocks' entries;
+ *   HGL_BLOCKS_AUTO    (default) sparse when the blocks' entries, counted once per
+ *                      build setup, are at most 1/512 of their dense size (a sparse
+ *                      entry costs a row gather, ~400x a dense entry on the GEMM).
+ * Both compute the same products (up to the BF16 rounding of the dense route).
+ */
+#define HGL_BLOCKS_AUTO   0
+#define HGL_BLOCKS_DENSE  1
+#define HGL_BLOCKS_SPARSE 2
+hgl_status hgl_set_block_product(hgl_graph* g, int32_t mode);
 
 /* Release a preconditioner (NULL is a no-op). */
 void hgl_precond_destroy(hgl_precond* P);

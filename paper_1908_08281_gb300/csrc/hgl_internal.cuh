@@ -107,6 +107,7 @@ struct hgl_graph {
   hgl::Buffer misc;            // gradient vectors (ex[m], phi[n])
   hgl::Buffer step;            // adaptive-step vectors (grad, w_old, projection work)
   hgl::Buffer rsvd;            // block rSVD work space (dense blocks, bases, Grams)
+  int block_product = HGL_BLOCKS_AUTO;  // route of the rSVD's products Theta_bb S
   int chunk_cols = 0;          // operator column chunk (0 = library default)
   // hyperedges in decreasing size order; the first nheavy (size > HEAVY_ROW) are
   // processed by a whole thread block each, the rest by one warp each in this order

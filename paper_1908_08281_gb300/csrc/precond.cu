@@ -15,13 +15,15 @@ namespace hgl {
 namespace {
 
 __global__ void k_gains(int nb, int k, int lpad, const double* __restrict__ ev_in, const int32_t* __restrict__ kb,
-                        double lam, double* __restrict__ ev_out, double* __restrict__ gain) {
+                        double lam, double* __restrict__ ev_out, double* __restrict__ gain,
+                        float* __restrict__ gain32) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nb * k; q += gridDim.x * blockDim.x) {
     const int b = q / k, r = q % k;
     double e = r < kb[b] ? ev_in[(int64_t)b * lpad + r] : 0.0;
     e = e < 0.0 ? 0.0 : (e > 1.0 ? 1.0 : e);  // spec(Theta_bb) lies in [0, 1]
     ev_out[q] = e;
     gain[q] = r < kb[b] ? e / ((1.0 + lam) * (1.0 + lam - e)) : 0.0;
+    if (gain32) gain32[q] = (float)gain[q];
   }
 }
 
@@ -470,7 +472,8 @@ __global__ void k_export_q(const float* __restrict__ Qf, const double* __restric
 }  // namespace
 
 hgl_status precond_gains_launch(hgl_precond* P, const double* ev_lpad, int lpad, cudaStream_t st) {
-  hgl::count_launch(); k_gains<<<(P->nb * P->k + 255) / 256, 256, 0, st>>>(P->nb, P->k, lpad, ev_lpad, P->d_kb, P->lam, P->ev, P->gain);
+  hgl::count_launch(); k_gains<<<(P->nb * P->k + 255) / 256, 256, 0, st>>>(P->nb, P->k, lpad, ev_lpad, P->d_kb, P->lam, P->ev, P->gain,
+                                                                             P->gain32);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -536,6 +539,14 @@ hgl_status precond_apply_launch(const hgl_precond* Pc, const hgl_graph* g, const
 }
 
 }  // namespace hgl
+
+extern "C" hgl_status hgl_set_block_product(hgl_graph* g, int32_t mode) {
+  if (!g) return hgl::record_error(HGL_ERR_INVALID_ARG, "graph is NULL");
+  if (mode != HGL_BLOCKS_AUTO && mode != HGL_BLOCKS_DENSE && mode != HGL_BLOCKS_SPARSE)
+    return hgl::record_error(HGL_ERR_INVALID_ARG, "unknown block product route %d", (int)mode);
+  g->block_product = mode;
+  return HGL_OK;
+}
 
 extern "C" hgl_status hgl_block_rsvd(const hgl_graph* g, const double* w, double lam, const int64_t* block_ptr,
                                      int32_t nblocks, int32_t k, int32_t p, int32_t q, uint64_t seed,

@@ -43,6 +43,7 @@ struct hgl_precond {
   int kp = 0;
   int64_t n4 = 0;
   float *Qh = nullptr, *Ql = nullptr, *QTh = nullptr, *QTl = nullptr;
+  float* gain32 = nullptr;       // the gains in FP32 (nb x k)
   int32_t* blk_order = nullptr;  // blocks by decreasing size
   int32_t* d_err = nullptr;      // set by a tensor-core kernel that gave up a wait
   CUtensorMap mQh, mQl, mQTh, mQTl;

@@ -84,15 +84,16 @@ k_tc_split(int64_t n, int64_t n4, int k, const float* __restrict__ Q, float* __r
 // ---------------------------------------------------------------------------
 // Projection.  Work unit = (block b, 128-column tile); units run in decreasing block
 // size over persistent CTAs.  Per step of 32 block rows:
-//   warp 0 (one lane): TMA of the R rows (32 x 128 FP32, unswizzled) into a deep ring
-//          of R stages (the DRAM stream: enough bytes in flight to cover its latency);
+//   warp 0 (one lane): TMA of the R rows (32 x 128 FP32, unswizzled) into a ring of R
+//          stages;
 //   warp 3 (one lane): TMA of Q_b^T hi/lo (KP x 32, K-major, 128-byte swizzle) into a
-//          ring of operand stages;
+//          ring of B stages (both rings deep enough to cover the DRAM latency: every
+//          step waits on both streams);
 //   warps 4-7 (thread t = panel column j): read column j of the staged rows, zero the
 //          rows outside the block, accumulate r.r, split into TF32 hi + lo and write
 //          them transposed (row t of a K-major 128 x 32 tile, 128-byte swizzle) into
-//          the operand stage (lo is left for the MMA to truncate to TF32: its error,
-//          2^-10 of lo, is 2^-21 of the element);
+//          a ring of two A stages (lo is left for the MMA to truncate to TF32: its
+//          error, 2^-10 of lo, is 2^-21 of the element);
 //   warp 1 (one lane): 4 K-substeps x 3 MMAs  D[j, i] += A[j, :] B[i, :]  (D = C^T, M =
 //          128 columns, N = KP ranks, accumulated in TMEM over the whole block).
 // Epilogue (warps 4-7, lane = column j): C[:, j] from TMEM, c_i = g_i C_ij split into
@@ -102,7 +103,7 @@ struct PjArgs {
   const int64_t* v0;
   const int32_t* rows;
   int nb, nct, c, k;
-  const double* gain;
+  const float* gain;  // FP32 copy, nb x k
   double inv1l;
   float* Ch;
   float* Cl;
@@ -112,18 +113,15 @@ struct PjArgs {
   int* err;
 };
 
-constexpr int PJ_RSTAGES = 6;   // R stages (16 KB each)
-constexpr int PJ_ABSTAGES = 2;  // operand stages (A hi/lo + B hi/lo)
+constexpr int PJ_RSTAGES = 5;  // R stages (16 KB each)
+constexpr int PJ_BSTAGES = 5;  // Q^T hi/lo stages (2 x KP x 128 bytes)
+constexpr int PJ_ASTAGES = 2;  // built R^T hi/lo stages (32 KB each)
 constexpr uint32_t PJ_R_BYTES = PJ_ROWS * PJ_COLS * 4;
-constexpr uint32_t PJ_A_BYTES = PJ_COLS * 128;
+constexpr uint32_t PJ_A_BYTES = PJ_COLS * 128;  // one split
 
 template <int KP>
-__host__ __device__ constexpr uint32_t pj_ab_bytes() {
-  return 2 * PJ_A_BYTES + 2 * KP * 128;
-}
-template <int KP>
 __host__ __device__ constexpr uint32_t pj_smem_bytes() {
-  return 1024 + PJ_RSTAGES * PJ_R_BYTES + PJ_ABSTAGES * pj_ab_bytes<KP>() + 256;
+  return 1024 + PJ_RSTAGES * PJ_R_BYTES + PJ_BSTAGES * 2 * KP * 128 + PJ_ASTAGES * 2 * PJ_A_BYTES + 256;
 }
 
 // One 32-row step of the builders: column t of the staged rows, rows [lo, hi) kept.
@@ -156,22 +154,25 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
              const __grid_constant__ CUtensorMap mapQTl, PjArgs a) {
   if (a.run_flag && *a.run_flag == 0) return;
   constexpr uint32_t B_BYTES = KP * 128;  // per split
-  constexpr uint32_t AB = pj_ab_bytes<KP>();
+  constexpr uint32_t BS = 2 * B_BYTES;    // one B stage
+  constexpr uint32_t AS = 2 * PJ_A_BYTES; // one A stage
   constexpr uint32_t ACC_COLS = KP;
   constexpr uint32_t TMEM_COLS = 2 * KP;
   constexpr uint32_t IDESC = umma::idesc_tf32_f32(PJ_COLS, KP);
-  static_assert(PJ_R_BYTES % 1024 == 0 && AB % 1024 == 0, "stages must keep 1024-byte alignment");
+  static_assert(PJ_R_BYTES % 1024 == 0 && BS % 1024 == 0 && AS % 1024 == 0, "stages must keep 1024-byte alignment");
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sR = smem;
-  uint8_t* sAB = smem + PJ_RSTAGES * PJ_R_BYTES;
-  uint64_t* r_full = reinterpret_cast<uint64_t*>(sAB + PJ_ABSTAGES * AB);
+  uint8_t* sB = sR + PJ_RSTAGES * PJ_R_BYTES;
+  uint8_t* sA = sB + PJ_BSTAGES * BS;
+  uint64_t* r_full = reinterpret_cast<uint64_t*>(sA + PJ_ASTAGES * AS);
   uint64_t* r_empty = r_full + PJ_RSTAGES;
   uint64_t* b_full = r_empty + PJ_RSTAGES;
-  uint64_t* a_full = b_full + PJ_ABSTAGES;
-  uint64_t* ab_empty = a_full + PJ_ABSTAGES;
-  uint64_t* acc_full = ab_empty + PJ_ABSTAGES;  // 2
+  uint64_t* b_empty = b_full + PJ_BSTAGES;
+  uint64_t* a_full = b_empty + PJ_BSTAGES;
+  uint64_t* a_empty = a_full + PJ_ASTAGES;
+  uint64_t* acc_full = a_empty + PJ_ASTAGES;  // 2
   uint64_t* acc_empty = acc_full + 2;           // 2
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
 
@@ -184,10 +185,13 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       mbar_init(r_full + s, 1);
       mbar_init(r_empty + s, 4);  // one arrival per builder warp
     }
-    for (int s = 0; s < PJ_ABSTAGES; ++s) {
+    for (int s = 0; s < PJ_BSTAGES; ++s) {
       mbar_init(b_full + s, 1);
+      mbar_init(b_empty + s, 1);
+    }
+    for (int s = 0; s < PJ_ASTAGES; ++s) {
       mbar_init(a_full + s, 4);
-      mbar_init(ab_empty + s, 1);
+      mbar_init(a_empty + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
@@ -201,7 +205,11 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
+  // units in decreasing block size, dealt to the CTAs in rounds of gridDim.x that
+  // alternate direction (every full odd round reversed), which evens out the CTAs' rows
   auto unit_rows = [&](int u, int& b, int& ct, int64_t& b0, int64_t& bend, int64_t& rs, int& nsteps) {
+    const int G = (int)gridDim.x, r = u / G;
+    if ((r & 1) && (r + 1) * G <= nunits) u = r * G + (G - 1 - (u - r * G));
     b = a.blk_order[u / a.nct];
     ct = u % a.nct;
     b0 = a.v0[b];
@@ -214,9 +222,9 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
     // ---------------- TMA producers: R (warp 0), Q^T hi/lo (warp 3) ----------------
     if (lane == 0) {
       const bool rprod = warp == 0;
-      const int nst = rprod ? PJ_RSTAGES : PJ_ABSTAGES;
+      const int nst = rprod ? PJ_RSTAGES : PJ_BSTAGES;
       uint64_t* full = rprod ? r_full : b_full;
-      uint64_t* empty = rprod ? r_empty : ab_empty;
+      uint64_t* empty = rprod ? r_empty : b_empty;
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -234,8 +242,8 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
             mbar_arrive_expect_tx(full + stage, PJ_R_BYTES);
             tma_load_2d(sR + stage * PJ_R_BYTES, &mapR, full + stage, ct * PJ_COLS, row);
           } else {
-            uint8_t* sb = sAB + stage * AB + 2 * PJ_A_BYTES;
-            mbar_arrive_expect_tx(full + stage, 2 * B_BYTES);
+            uint8_t* sb = sB + stage * BS;
+            mbar_arrive_expect_tx(full + stage, BS);
             tma_load_2d(sb, &mapQTh, full + stage, row, 0);
             tma_load_2d(sb + B_BYTES, &mapQTl, full + stage, row, 0);
           }
@@ -249,8 +257,8 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      int bstage = 0, astage = 0;
+      uint32_t bphase = 0, aphase = 0;
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true;
@@ -262,15 +270,14 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)acc * ACC_COLS;
         for (int s = 0; s < nsteps; ++s) {
-          if (!mbar_wait(b_full + stage, phase, a.err) || !mbar_wait(a_full + stage, phase, a.err)) {
+          if (!mbar_wait(b_full + bstage, bphase, a.err) || !mbar_wait(a_full + astage, aphase, a.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t sa = smem_u32(sAB + stage * AB);
+          const uint32_t sa = smem_u32(sA + astage * AS), sb = smem_u32(sB + bstage * BS);
           const uint64_t ah = smem_desc_sw128(sa), al = smem_desc_sw128(sa + PJ_A_BYTES);
-          const uint64_t bh = smem_desc_sw128(sa + 2 * PJ_A_BYTES);
-          const uint64_t bl = smem_desc_sw128(sa + 2 * PJ_A_BYTES + B_BYTES);
+          const uint64_t bh = smem_desc_sw128(sb), bl = smem_desc_sw128(sb + B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < PJ_ROWS / 8; ++kk) {
             // 8 TF32 elements (32 bytes) along K per MMA inside the 128-byte swizzled row
@@ -279,10 +286,15 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
             umma::mma_tf32(d_tmem, ah + off, bl + off, IDESC, 1u);
             umma::mma_tf32(d_tmem, al + off, bh + off, IDESC, 1u);
           }
-          umma::mma_commit(ab_empty + stage);
-          if (++stage == PJ_ABSTAGES) {
-            stage = 0;
-            phase ^= 1;
+          umma::mma_commit(b_empty + bstage);
+          umma::mma_commit(a_empty + astage);
+          if (++bstage == PJ_BSTAGES) {
+            bstage = 0;
+            bphase ^= 1;
+          }
+          if (++astage == PJ_ASTAGES) {
+            astage = 0;
+            aphase ^= 1;
           }
         }
         if (!ok) break;
@@ -308,12 +320,12 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       unit_rows(u, b, ct, b0, bend, rs, nsteps);
       double rr = 0.0;
       for (int s = 0; s < nsteps; ++s) {
-        if (!mbar_wait(r_full + rstage, rphase, a.err) || !mbar_wait(ab_empty + astage, aphase ^ 1, a.err)) {
+        if (!mbar_wait(r_full + rstage, rphase, a.err) || !mbar_wait(a_empty + astage, aphase ^ 1, a.err)) {
           ok = false;
           break;
         }
         const float* stg = reinterpret_cast<const float*>(sR + rstage * PJ_R_BYTES);
-        uint8_t* ah = sAB + astage * AB;
+        uint8_t* ah = sA + astage * AS;
         const int64_t row0 = rs + (int64_t)s * PJ_ROWS;
         const int lo = (int)(b0 > row0 ? b0 - row0 : 0);
         const int hi = (int)(bend - row0 < PJ_ROWS ? bend - row0 : PJ_ROWS);
@@ -331,7 +343,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
           rstage = 0;
           rphase ^= 1;
         }
-        if (++astage == PJ_ABSTAGES) {
+        if (++astage == PJ_ASTAGES) {
           astage = 0;
           aphase ^= 1;
         }
@@ -357,26 +369,25 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
         acc_phase ^= 1;
       }
       const int j = ct * PJ_COLS + t;
-      const double* gb = a.gain + (int64_t)b * a.k;
-      double rz = rr * a.inv1l;
+      const float* gb = a.gain + (int64_t)b * a.k;
       float* ch = a.Ch + ((int64_t)b * a.c128 + j) * KP;
       float* cl = a.Cl + ((int64_t)b * a.c128 + j) * KP;
+      float gcc = 0.f;  // sum_i g_i C_ij^2: 64 non-negative terms, FP32 is plenty
 #pragma unroll
       for (int q = 0; q < KP / 4; ++q) {
         float h[4], l[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int i = 4 * q + e;
-          const double g = i < a.k ? gb[i] : 0.0;
-          rz += g * (double)cv[i] * (double)cv[i];
-          const float x = (float)(g * (double)cv[i]);
+          const float x = (i < a.k ? gb[i] : 0.f) * cv[i];
+          gcc = fmaf(x, cv[i], gcc);
           h[e] = tf32_round(x);
           l[e] = tf32_round(x - h[e]);
         }
         *reinterpret_cast<float4*>(ch + 4 * q) = make_float4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<float4*>(cl + 4 * q) = make_float4(l[0], l[1], l[2], l[3]);
       }
-      if (a.rz && j < a.c) a.rz[(int64_t)b * a.c + j] = rz;
+      if (a.rz && j < a.c) a.rz[(int64_t)b * a.c + j] = rr * a.inv1l + (double)gcc;
     }
   }
   tc_fence_before();
@@ -730,7 +741,7 @@ hgl_status tc_apply(hgl_precond* P, const float* R, int64_t ldr, float* Z, int64
     attr_set = true;
   }
   const int sms = device_sm_count();
-  PjArgs pa{P->blk_order, P->d_v0, P->d_rows, P->nb, (int)(c128 / PJ_COLS), c, P->k, P->gain,
+  PjArgs pa{P->blk_order, P->d_v0, P->d_rows, P->nb, (int)(c128 / PJ_COLS), c, P->k, P->gain32,
             1.0 / (1.0 + P->lam), Ch, Cl, c128, rz, run_flag, P->d_err};
   ExArgs ea{P->exp_block, P->exp_tile, P->nexp, P->d_v0, P->d_rows, Z, ldz, c, (c + EX_COLS - 1) / EX_COLS,
             c128, (float)(1.0 / (1.0 + P->lam)), run_flag, P->d_err};

@@ -105,12 +105,15 @@ struct Work {
   double* ev = nullptr;   // nb x lpad
   int32_t* fail = nullptr;
   int* err = nullptr;
+  bool sparse = false;    // Theta_bb S from the incidence lists (no dense blocks)
 };
 
 inline size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 
-hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, int l, int lpad, int dtype, Work* w) {
+hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, int l, int lpad, int dtype,
+                bool sparse, Work* w) {
   const bool bf16 = dtype == HGL_BF16;
+  w->sparse = sparse;
   w->v0.resize(nb);
   w->arow.resize(nb);
   w->koff.resize(nb);
@@ -148,7 +151,7 @@ hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, i
     off += a256(bytes);
     return o;
   };
-  const size_t oA = take(ea * (size_t)w->rows_tot * (size_t)w->ldA);
+  const size_t oA = take(sparse ? 0 : ea * (size_t)w->rows_tot * (size_t)w->ldA);
   const size_t oSt = take(ea * (size_t)lpad * (size_t)w->Ktot);
   const size_t oD = take(ed * (size_t)w->rows_tot * lpad);
   const size_t oQf = take(ed * (size_t)w->rows_tot * lpad);
@@ -215,9 +218,20 @@ hgl_status set_smem(F* fn, size_t bytes) {
   return HGL_OK;
 }
 
-// D = Theta_bb * S for all blocks (St holds S^T).
+// D = Theta_bb * S for all blocks: the grouped GEMM over the dense blocks (St holds
+// S^T), or on the sparse route the product straight from the incidence lists (Qf
+// holds S).
 template <int LP>
-hgl_status gemm(const Work& w, int dtype, int sms, cudaStream_t st) {
+hgl_status gemm(const hgl_graph* g, const Work& w, int dtype, int sms, cudaStream_t st) {
+  if (w.sparse) {
+    ProfScope prof(HGL_PROF_BLOCKSPMM, st);
+    hgl::count_launch();
+    rsvd::k_block_spmm<LP><<<sms * 8, 256, 0, st>>>(w.B, w.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx,
+                                                    g->s, g->t, static_cast<const float*>(w.Qf),
+                                                    static_cast<float*>(w.D));
+    HGL_CHECK_CUDA(cudaGetLastError());
+    return HGL_OK;
+  }
   const int nu = (int)w.unit_block.size();
   ProfScope prof(HGL_PROF_GEMM, st);
   if (dtype == HGL_BF16) {
@@ -306,6 +320,39 @@ hgl_status precond_validate(const hgl_graph* g, const int64_t* bp, int32_t nb, i
   return HGL_OK;
 }
 
+// Route of the products Theta_bb S on the BF16 path: the graph's setting, or by fill
+// (auto): the tcgen05 GEMM streams every dense block entry (2 bytes, 2 lpad flops),
+// measured at ~3e12 entries/s with lpad = 80; the sparse route gathers one basis row
+// (4 lpad bytes) per block entry after a binary search, measured at ~8e9 entries/s.
+// Sparse when the blocks' entries are at most 1/512 of their dense size.  Synchronous.
+static hgl_status block_route_sparse(hgl_graph* g, const int64_t* bp, int nb, cudaStream_t st, bool* sparse) {
+  if (g->block_product != HGL_BLOCKS_AUTO) {
+    *sparse = g->block_product == HGL_BLOCKS_SPARSE;
+    return HGL_OK;
+  }
+  double dense = 0.0;
+  for (int b = 0; b < nb; ++b) dense += (double)rup(bp[b + 1] - bp[b], 128) * (double)rup(bp[b + 1] - bp[b], 64);
+  void* mem = nullptr;
+  HGL_CHECK_CUDA(cudaMalloc(&mem, 8 * (size_t)(nb + 2)));
+  int64_t* d_bp = static_cast<int64_t*>(mem);
+  unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(d_bp + nb + 1);
+  unsigned long long cnt = 0;
+  cudaError_t e = cudaMemcpyAsync(d_bp, bp, 8 * (size_t)(nb + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 8, st);
+  if (e == cudaSuccess) {
+    hgl::count_launch();
+    rsvd::k_block_nnz<<<g->num_sms * 8, 256, 0, st>>>(g->n, nb, d_bp, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                      g->csc_idx, d_cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (e != cudaSuccess) return cuda_error(e, "block fill count", __FILE__, __LINE__);
+  *sparse = 512.0 * (double)cnt <= dense;
+  return HGL_OK;
+}
+
 void precond_plan_destroy(PrecondPlan* pl) {
   if (!pl) return;
   if (pl->P) hgl_precond_destroy(pl->P);
@@ -326,7 +373,13 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
   if (!pl) return record_error(HGL_ERR_OOM, "host allocation failed");
   pl->dtype = gemm_dtype;
   pl->q = q;
-  hgl_status s_ = plan(g, own_space ? pl->own : g->rsvd, bp, nb, k, l, lpad, gemm_dtype, &pl->wk);
+  bool sparse = false;
+  hgl_status s_ = gemm_dtype == HGL_BF16 ? block_route_sparse(g, bp, nb, st, &sparse) : HGL_OK;
+  if (s_ != HGL_OK) {
+    precond_plan_destroy(pl);
+    return s_;
+  }
+  s_ = plan(g, own_space ? pl->own : g->rsvd, bp, nb, k, l, lpad, gemm_dtype, sparse, &pl->wk);
   if (s_ != HGL_OK) {
     precond_plan_destroy(pl);
     return s_;
@@ -399,6 +452,7 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
   const size_t tcq = P->tc ? 4 * (size_t)g->n * P->kp : 0;
   const size_t tcqt = P->tc ? 4 * (size_t)P->kp * P->n4 : 0;
   const size_t oQh = take(tcq), oQl = take(tcq), oQTh = take(tcqt), oQTl = take(tcqt);
+  const size_t oG32 = take(P->tc ? 4 * (size_t)nb * k : 0);
   const size_t oOrd = take(4 * (size_t)nb);
   const size_t oErr = take(4);
   std::vector<int32_t> order(nb);
@@ -429,6 +483,7 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
     P->Ql = reinterpret_cast<float*>(base + oQl);
     P->QTh = reinterpret_cast<float*>(base + oQTh);
     P->QTl = reinterpret_cast<float*>(base + oQTl);
+    P->gain32 = reinterpret_cast<float*>(base + oG32);
   }
   P->blk_order = reinterpret_cast<int32_t*>(base + oOrd);
   P->d_err = reinterpret_cast<int32_t*>(base + oErr);
@@ -477,8 +532,14 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
   HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
   const bool bf16 = gemm_dtype == HGL_BF16;
 
-  // dense diagonal blocks and the Gaussian start basis
-  if (bf16) {
+  // dense diagonal blocks and the Gaussian start basis (sparse route: the basis only,
+  // in the row layout the sparse product reads)
+  if (bf16 && wk.sparse) {
+    HGL_LPAD_SWITCH(lpad, {
+      hgl::count_launch();
+      rsvd::k_omega_rows<LP><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, seed, seed_dev, static_cast<float*>(wk.Qf));
+    });
+  } else if (bf16) {
     hgl::count_launch(2);
     rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
                                                             g->csc_idx, g->s, g->t,
@@ -498,12 +559,12 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
   hgl_status s_ = HGL_OK;
   HGL_LPAD_SWITCH(lpad, {
     for (int i = 0; i < nprod && s_ == HGL_OK; ++i) {
-      s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+      s_ = gemm<LP>(g, wk, gemm_dtype, sms, st);
       if (s_ == HGL_OK)
-        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, true)
+        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, !wk.sparse)
                   : cholqr2<double, double, LP>(wk, gemm_dtype, sms, st, true);
     }
-    if (s_ == HGL_OK) s_ = gemm<LP>(wk, gemm_dtype, sms, st);
+    if (s_ == HGL_OK) s_ = gemm<LP>(g, wk, gemm_dtype, sms, st);
     if (s_ == HGL_OK) {
       // T = S^T (Theta S), eigendecomposition, Ritz vectors
       s_ = bf16 ? gram<float, LP>(wk, static_cast<const float*>(wk.Qf), static_cast<const float*>(wk.D), st)

@@ -142,6 +142,123 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Sparse route for blocks that hold few of Theta's entries: Theta_bb S straight from
+// the incidence lists, without dense blocks.
+//   Theta_bb[u, u] = s_u^2 sum_{e ni u} t_e
+//   Theta_bb[u, v] = s_u s_v sum_{e ni u, v} t_e      (u != v, both in block b)
+// The members of a hyperedge that fall in block b form one run of its sorted member
+// list, found by two binary searches (as in the assembly above).
+// ---------------------------------------------------------------------------
+
+// Run [lo, hi) of hyperedge e's sorted members inside [v0, v1).
+__device__ __forceinline__ void member_run(const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
+                                           int32_t e, int64_t v0, int64_t v1, int64_t* lo, int64_t* hi) {
+  int64_t a = csc_ptr[e], z = csc_ptr[e + 1];
+  const int64_t me = z;
+  while (a < z) {
+    const int64_t mid = (a + z) >> 1;
+    if (csc_idx[mid] < v0) a = mid + 1; else z = mid;
+  }
+  *lo = a;
+  z = me;
+  while (a < z) {
+    const int64_t mid = (a + z) >> 1;
+    if (csc_idx[mid] < v1) a = mid + 1; else z = mid;
+  }
+  *hi = a;
+}
+
+// Entries of all diagonal blocks (with one per hyperedge for repeated pairs), summed
+// into *count: for every vertex u, the length of its block's run in each of its
+// hyperedges.  bp: the nb + 1 block boundaries.
+static __global__ void k_block_nnz(int64_t n, int nb, const int64_t* __restrict__ bp, const int64_t* __restrict__ csr_ptr,
+                            const int32_t* __restrict__ csr_idx, const int64_t* __restrict__ csc_ptr,
+                            const int32_t* __restrict__ csc_idx, unsigned long long* __restrict__ count) {
+  unsigned long long local = 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int b = find_block(bp, nb, u);
+    for (int64_t q = csr_ptr[u]; q < csr_ptr[u + 1]; ++q) {
+      int64_t lo, hi;
+      member_run(csc_ptr, csc_idx, csr_idx[q], bp[b], bp[b + 1], &lo, &hi);
+      local += (unsigned long long)(hi - lo);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(count, local);
+}
+
+// D = Theta_bb S for every block; S and D in the dense route's row layout (block b's
+// row i at arow[b] + i, padding rows zero), LP FP32 columns.  One warp per row:
+// lanes split the row's columns; for the off-diagonal terms the lanes take 32 of u's
+// hyperedges at a time, search their runs, and the warp adds the rows of the runs
+// longer than one, hyperedge by hyperedge in CSR order (a fixed summation order).
+template <int LP>
+__global__ void __launch_bounds__(256)
+k_block_spmm(Blocks B, int64_t rows_tot, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+             const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx, const double* __restrict__ s,
+             const double* __restrict__ t, const float* __restrict__ S, float* __restrict__ D) {
+  constexpr int PL = (LP + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows_tot; r += nwarps) {
+    const int b = find_block(B.arow, B.nb, r);
+    const int64_t i = r - B.arow[b];
+    float* drow = D + r * LP;
+    if (i >= B.rows[b]) {
+#pragma unroll
+      for (int p = 0; p < PL; ++p)
+        if (lane + 32 * p < LP) drow[lane + 32 * p] = 0.f;
+      continue;
+    }
+    const int64_t v0 = B.v0[b], v1 = v0 + B.rows[b];
+    const int64_t u = v0 + i;
+    const double su = s[u];
+    const int64_t beg = csr_ptr[u], end = csr_ptr[u + 1];
+    double d = 0.0;
+    for (int64_t q = beg + lane; q < end; q += 32) d += t[csr_idx[q]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    const float fd = (float)(su * su * d);
+    const float* srow = S + r * LP;
+    float acc[PL];
+#pragma unroll
+    for (int p = 0; p < PL; ++p) acc[p] = lane + 32 * p < LP ? fd * srow[lane + 32 * p] : 0.f;
+    for (int64_t q0 = beg; q0 < end; q0 += 32) {
+      const int64_t q = q0 + lane;
+      int64_t lo = 0, hi = 0;
+      int32_t e = 0;
+      if (q < end) {
+        e = csr_idx[q];
+        member_run(csc_ptr, csc_idx, e, v0, v1, &lo, &hi);
+      }
+      unsigned todo = __ballot_sync(0xffffffffu, hi - lo > 1);
+      while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int64_t l2 = __shfl_sync(0xffffffffu, lo, src);
+        const int64_t h2 = __shfl_sync(0xffffffffu, hi, src);
+        const int32_t e2 = __shfl_sync(0xffffffffu, e, src);
+        const double f = su * t[e2];
+        for (int64_t p2 = l2; p2 < h2; ++p2) {
+          const int32_t v = csc_idx[p2];
+          if (v == u) continue;
+          const float fv = (float)(f * s[v]);
+          const float* vrow = S + (B.arow[b] + (v - v0)) * LP;
+#pragma unroll
+          for (int p = 0; p < PL; ++p)
+            if (lane + 32 * p < LP) acc[p] = fmaf(fv, vrow[lane + 32 * p], acc[p]);
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < PL; ++p)
+      if (lane + 32 * p < LP) drow[lane + 32 * p] = acc[p];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC 2011) and the Gaussian test matrix Omega.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
@@ -207,6 +324,25 @@ __global__ void k_omega(Blocks B, uint64_t seed_arg, const uint64_t* __restrict_
     if (i < B.rows[b] && 2 * p < B.lb[b]) omega_pair<TB>(B.v0[b] + i, p, seed, &z0, &z1);
     St[(int64_t)(2 * p) * B.Ktot + col] = from_double<TB>(z0);
     St[(int64_t)(2 * p + 1) * B.Ktot + col] = from_double<TB>(2 * p + 1 < B.lb[b] ? z1 : 0.0);
+  }
+}
+
+// Omega in the row layout of the sparse route: S[arow_b + i, c] (FP32, LP columns) for
+// the same Gaussian numbers as k_omega (zero beyond l_b and on padding rows).
+template <int LP>
+__global__ void k_omega_rows(Blocks B, int64_t rows_tot, uint64_t seed_arg, const uint64_t* __restrict__ seed_dev,
+                             float* __restrict__ S) {
+  const uint64_t seed = seed_dev ? *seed_dev : seed_arg;
+  const int64_t total = rows_tot * (LP / 2);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / (LP / 2);
+    const int p = (int)(q % (LP / 2));
+    const int b = find_block(B.arow, B.nb, r);
+    const int64_t i = r - B.arow[b];
+    double z0 = 0.0, z1 = 0.0;
+    if (i < B.rows[b] && 2 * p < B.lb[b]) omega_pair<float>(B.v0[b] + i, p, seed, &z0, &z1);
+    S[r * LP + 2 * p] = (float)z0;
+    S[r * LP + 2 * p + 1] = 2 * p + 1 < B.lb[b] ? (float)z1 : 0.f;
   }
 }
 

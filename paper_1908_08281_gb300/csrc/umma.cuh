@@ -64,17 +64,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of a barrier.  Gives up after ~2 s, or at once when another
-// role has already flagged an error; on give-up records code 1 in *err and returns
-// false so the caller can leave its loop.
+// Wait for phase `parity` of a barrier.  Gives up after ~2 s, or soon after another
+// role has flagged an error; on give-up records code 1 in *err and returns false so
+// the caller can leave its loop.  The error word and the clock are read only every 64
+// polls (each poll is a try_wait, which itself suspends for a while): a global read on
+// every poll would delay the waiter's wake-up by a memory latency.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = clock64();
-  for (;;) {
+  for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*(volatile int*)err != 0) return false;
-    if (clock64() - t0 > SPIN_CYCLES) {
-      atomicExch(err, 1);
-      return false;
+    if ((it & 63u) == 0) {
+      if (*(volatile int*)err != 0) return false;
+      if (clock64() - t0 > SPIN_CYCLES) {
+        atomicExch(err, 1);
+        return false;
+      }
     }
   }
 }

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "hgl_precond_export": (_I32, [_P, _I32, _P, _P, ctypes.POINTER(_I32), _P]),
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_precond_tensor_cores": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
+    "hgl_set_block_product": (_I32, [_P, _I32]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
@@ -122,10 +123,12 @@ def launch_count() -> int:
 
 
 PROF_OPERATOR, PROF_RESIDUAL, PROF_GEMM, PROF_GRADIENT = 0, 1, 2, 3
-PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT, PROF_OPRESID = 4, 5, 6, 7, 8
+PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT, PROF_OPRESID, PROF_BLOCKSPMM = 4, 5, 6, 7, 8, 9
+HGL_BLOCKS_AUTO, HGL_BLOCKS_DENSE, HGL_BLOCKS_SPARSE = 0, 1, 2
 PROF_NAMES = {0: "operator apply", 1: "pair-arithmetic residual", 2: "grouped block GEMM (tcgen05)",
               3: "weight gradient", 4: "preconditioner apply", 5: "block rSVD build (all)",
-              6: "CG vector kernels", 7: "simplex projection", 8: "residual by one operator pass"}
+              6: "CG vector kernels", 7: "simplex projection", 8: "residual by one operator pass",
+              9: "sparse block products (rSVD)"}
 
 
 def profile_enable(on: bool = True):
@@ -370,6 +373,13 @@ def precond_apply(P: Precond, R: torch.Tensor, Z: torch.Tensor | None = None, st
     pz, ldz, _ = _panel(Z, "Z")
     _check(lib().hgl_precond_apply(P.handle, pr, ldr, pz, ldz, c, dt, _stream(stream)))
     return Z
+
+
+def set_block_product(g: Graph, mode: int):
+    """Route of the block rSVD's products Theta_bb S for later builds on g:
+    HGL_BLOCKS_DENSE (tcgen05 GEMM on dense BF16 blocks), HGL_BLOCKS_SPARSE (from the
+    incidence lists) or HGL_BLOCKS_AUTO (by the blocks' fill)."""
+    _check(lib().hgl_set_block_product(g.handle, mode))
 
 
 def precond_tensor_cores(P: Precond, on: bool) -> bool:

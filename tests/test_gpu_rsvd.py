@@ -42,6 +42,46 @@ def _panel(a, dtype=torch.float64):
 K, P_, Q_, SEED = 8, 4, 2, 1234
 
 
+def _route_used(g, w, bp, k=8):
+    """Which products a BF16 build runs: (tcgen05 GEMM launches, sparse product launches)."""
+    hgl.profile_enable(True)
+    hgl.block_rsvd(g, w, 0.5, bp, k, 4, 1, SEED, gemm_dtype=hgl.HGL_BF16)
+    torch.cuda.synchronize()
+    used = (hgl.profile_read(hgl.PROF_GEMM)[1], hgl.profile_read(hgl.PROF_BLOCKSPMM)[1])
+    hgl.profile_enable(False)
+    return used
+
+
+def test_block_product_route_by_fill():
+    """HGL_BLOCKS_AUTO: small hyperedges with random members put few of Theta's entries
+    inside large diagonal blocks (sparse route); hyperedges drawn inside one block fill
+    them (dense route, the tcgen05 GEMM); the explicit settings override."""
+    rng = np.random.default_rng(8)
+    n, m = 40000, 60000
+    mem = np.sort(np.stack([rng.choice(n, 3, replace=False) for _ in range(m)]), axis=1).ravel()
+    g = hgl.build_incidence(n, m, np.arange(0, 3 * m + 1, 3, dtype=np.int64), mem.astype(np.int32))
+    wt = torch.full((m,), 1.0 / m, dtype=torch.float64, device=DEV)
+    bp = [0, 10000, 20000, 30000, 40000]
+    # q = 1: 1 + 2q products in the range finder and one for the Rayleigh-Ritz matrix
+    assert _route_used(g, wt, bp) == (0, 4)
+    hgl.set_block_product(g, hgl.HGL_BLOCKS_DENSE)
+    assert _route_used(g, wt, bp) == (4, 0)
+    hgl.set_block_product(g, hgl.HGL_BLOCKS_AUTO)
+    # community hypergraph: 4 blocks of 512 vertices, 300 hyperedges of 40 members each
+    rng = np.random.default_rng(9)
+    n, nbk, size = 2048, 4, 512
+    ptr, mem = [0], []
+    for e in range(1200):
+        b = e % nbk
+        mem.extend(sorted(rng.choice(size, 40, replace=False) + b * size))
+        ptr.append(len(mem))
+    gc = hgl.build_incidence(n, 1200, np.asarray(ptr, np.int64), np.asarray(mem, np.int32))
+    wc = torch.full((1200,), 1.0 / 1200, dtype=torch.float64, device=DEV)
+    assert _route_used(gc, wc, [0, 512, 1024, 1536, 2048]) == (4, 0)
+    with pytest.raises(hgl.HglError):
+        hgl.set_block_product(g, 7)
+
+
 def test_rsvd_fp64_matches_oracle():
     wl, d, H, w, g = _setup()
     bp = d["block_ptr"]
@@ -65,13 +105,18 @@ def test_rsvd_fp64_matches_oracle():
     assert np.abs(Z32 - Zo).max() <= 1e-5 * np.abs(Zo).max()
 
 
+@pytest.mark.parametrize("route", [hgl.HGL_BLOCKS_DENSE, hgl.HGL_BLOCKS_SPARSE])
 @pytest.mark.parametrize("k,p", [(8, 4), (16, 8), (40, 8), (64, 10)])
-def test_rsvd_bf16_tensor_cores_vs_fp64(k, p):
+def test_rsvd_bf16_tensor_cores_vs_fp64(k, p, route):
+    """The BF16 path's factors against the FP64 path's (same Omega): dense BF16 blocks on
+    the tcgen05 GEMM, or the FP32 products from the incidence lists."""
     wl, d, H, w, g = _setup(n=12000, m=20000, seed=2)
     bp = d["block_ptr"]
     wt = torch.tensor(w, device=DEV)
     P64 = hgl.block_rsvd(g, wt, wl.lam, bp, k, p, Q_, SEED, gemm_dtype=hgl.HGL_FP64)
+    hgl.set_block_product(g, route)
     P16 = hgl.block_rsvd(g, wt, wl.lam, bp, k, p, Q_, SEED, gemm_dtype=hgl.HGL_BF16)
+    hgl.set_block_product(g, hgl.HGL_BLOCKS_AUTO)
     blocks = rsvd.block_theta(H, w, bp)
     worst = 0.0
     for b in range(len(bp) - 1):
@@ -89,8 +134,9 @@ def test_rsvd_bf16_tensor_cores_vs_fp64(k, p):
             r16 = np.linalg.norm(Tb @ q16 - q16 * e16, axis=0)
             r64 = np.linalg.norm(Tb @ q64 - q64 * e64, axis=0)
             assert (r16 <= r64 + 2e-2 * max(e64.max(), 1e-12)).all(), (b, r16.max(), r64.max())
-    # BF16 storage of Theta_bb and of the basis: a few units of 2^-8 in the Ritz values
-    assert worst <= 3e-2, worst
+    # BF16 storage of Theta_bb and of the basis: a few units of 2^-8 in the Ritz values;
+    # the sparse route keeps FP32 products
+    assert worst <= (3e-2 if route == hgl.HGL_BLOCKS_DENSE else 1e-3), worst
     rng = np.random.default_rng(4)
     Rn = rng.standard_normal((d["n"], 7))
     Z64 = hgl.precond_apply(P64, _panel(Rn)).cpu().numpy()
