@@ -571,14 +571,14 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
                 : gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
       if (bf16) {
         // FP32 rotations: the BF16 products bound the accuracy of T well above FP32's
-        const size_t jsm = 2 * sizeof(float) * LP * LP;
+        const size_t jsm = 2 * sizeof(float) * LP * (LP + 1);
         if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<float, LP>, jsm);
         if (s_ == HGL_OK) {
           hgl::count_launch();
           rsvd::k_jacobi<float, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 16, 1e-10);
         }
       } else {
-        const size_t jsm = 2 * sizeof(double) * LP * LP;
+        const size_t jsm = 2 * sizeof(double) * LP * (LP + 1);
         if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
         if (s_ == HGL_OK) {
           hgl::count_launch();

@@ -655,9 +655,11 @@ __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __r
 template <class TJ, int LPAD>
 __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restrict__ Tm, double* __restrict__ V,
                                                  double* __restrict__ evals, int max_sweeps, double tol2) {
+  // row stride LS = LPAD + 1 (odd): a warp walking down a column touches 32 banks
+  constexpr int LS = LPAD + 1;
   extern __shared__ __align__(16) uint8_t jsm_raw[];
-  TJ* A = reinterpret_cast<TJ*>(jsm_raw);   // LPAD x LPAD
-  TJ* W = A + LPAD * LPAD;                   // eigenvectors
+  TJ* A = reinterpret_cast<TJ*>(jsm_raw);   // LPAD x LS
+  TJ* W = A + LPAD * LS;                     // eigenvectors, LPAD x LS
   __shared__ TJ cs[LPAD / 2], sn[LPAD / 2];
   __shared__ int pp[LPAD / 2], qq[LPAD / 2];
   __shared__ double off_s, tot_s;
@@ -665,36 +667,38 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   const int b = blockIdx.x;
   const int lb = B.lb[b];
   const int n = (lb + 1) & ~1;  // even, a dummy index when lb is odd
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = 256 / 32;
   const double* Tb = Tm + (int64_t)b * LPAD * LPAD;
-  for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
-    const int i = q / LPAD, j = q % LPAD;
-    A[q] = (i < lb && j < lb) ? (TJ)(0.5 * (Tb[i * LPAD + j] + Tb[j * LPAD + i])) : TJ(0);
-    W[q] = (i == j) ? TJ(1) : TJ(0);
-  }
+  for (int i = warp; i < LPAD; i += NW)
+    for (int j = lane; j < LPAD; j += 32) {
+      A[i * LS + j] = (i < lb && j < lb) ? (TJ)(0.5 * (Tb[i * LPAD + j] + Tb[j * LPAD + i])) : TJ(0);
+      W[i * LS + j] = (i == j) ? TJ(1) : TJ(0);
+    }
   __syncthreads();
-  __shared__ double red_off[8], red_tot[8];
+  __shared__ double red_off[NW], red_tot[NW];
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     {
       double off = 0.0, tot = 0.0;
-      for (int q = threadIdx.x; q < lb * lb; q += blockDim.x) {
-        const int i = q / lb, j = q % lb;
-        const double a = (double)A[i * LPAD + j];
-        tot += a * a;
-        if (i != j) off += a * a;
-      }
+      for (int i = warp; i < lb; i += NW)
+        for (int j = lane; j < lb; j += 32) {
+          const double a = (double)A[i * LS + j];
+          tot += a * a;
+          if (i != j) off += a * a;
+        }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         off += __shfl_xor_sync(0xffffffffu, off, o);
         tot += __shfl_xor_sync(0xffffffffu, tot, o);
       }
-      if ((threadIdx.x & 31) == 0) {
-        red_off[threadIdx.x >> 5] = off;
-        red_tot[threadIdx.x >> 5] = tot;
+      if (lane == 0) {
+        red_off[warp] = off;
+        red_tot[warp] = tot;
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         double a = 0.0, t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 0; w < NW; ++w) {
           a += red_off[w];
           t += red_tot[w];
         }
@@ -718,9 +722,9 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
         qq[p] = z;
         TJ c = TJ(1), s = TJ(0);
         if (z < lb) {
-          const TJ apq = A[a * LPAD + z];
+          const TJ apq = A[a * LS + z];
           if (apq != TJ(0)) {
-            const TJ app = A[a * LPAD + a], aqq = A[z * LPAD + z];
+            const TJ app = A[a * LS + a], aqq = A[z * LS + z];
             const TJ theta = (aqq - app) / (TJ(2) * apq);
             const TJ tt = (theta >= TJ(0) ? TJ(1) : TJ(-1)) / (fabs(theta) + sqrt(theta * theta + TJ(1)));
             c = TJ(1) / sqrt(tt * tt + TJ(1));
@@ -731,30 +735,30 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
         sn[p] = s;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int q = threadIdx.x; q < (n / 2) * lb; q += blockDim.x) {
-        const int p = q / lb, col = q % lb;
+      // rows: A <- J^T A (a warp per pair, lanes along the row)
+      for (int p = warp; p < n / 2; p += NW) {
         const int a = pp[p], z = qq[p];
-        if (z < lb) {
-          const TJ c = cs[p], s = sn[p];
-          const TJ x = A[a * LPAD + col], y = A[z * LPAD + col];
-          A[a * LPAD + col] = c * x - s * y;
-          A[z * LPAD + col] = s * x + c * y;
+        if (z >= lb) continue;
+        const TJ c = cs[p], s = sn[p];
+        for (int col = lane; col < lb; col += 32) {
+          const TJ x = A[a * LS + col], y = A[z * LS + col];
+          A[a * LS + col] = c * x - s * y;
+          A[z * LS + col] = s * x + c * y;
         }
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int q = threadIdx.x; q < (n / 2) * lb; q += blockDim.x) {
-        const int p = q / lb, row = q % lb;
+      // columns: A <- A J, V <- V J (a warp per pair, lanes down the column)
+      for (int p = warp; p < n / 2; p += NW) {
         const int a = pp[p], z = qq[p];
-        if (z < lb) {
-          const TJ c = cs[p], s = sn[p];
-          const TJ x = A[row * LPAD + a], y = A[row * LPAD + z];
-          A[row * LPAD + a] = c * x - s * y;
-          A[row * LPAD + z] = s * x + c * y;
-          const TJ vx = W[row * LPAD + a], vy = W[row * LPAD + z];
-          W[row * LPAD + a] = c * vx - s * vy;
-          W[row * LPAD + z] = s * vx + c * vy;
+        if (z >= lb) continue;
+        const TJ c = cs[p], s = sn[p];
+        for (int row = lane; row < lb; row += 32) {
+          const TJ x = A[row * LS + a], y = A[row * LS + z];
+          A[row * LS + a] = c * x - s * y;
+          A[row * LS + z] = s * x + c * y;
+          const TJ vx = W[row * LS + a], vy = W[row * LS + z];
+          W[row * LS + a] = c * vx - s * vy;
+          W[row * LS + z] = s * vx + c * vy;
         }
       }
       __syncthreads();
@@ -762,10 +766,10 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   }
   // sort eigenvalues descending (selection by rank; ties broken by index)
   for (int i = threadIdx.x; i < lb; i += blockDim.x) {
-    const TJ di = A[i * LPAD + i];
+    const TJ di = A[i * LS + i];
     int rank = 0;
     for (int j = 0; j < lb; ++j) {
-      const TJ dj = A[j * LPAD + j];
+      const TJ dj = A[j * LS + j];
       if (dj > di || (dj == di && j < i)) ++rank;
     }
     order[rank] = i;
@@ -774,10 +778,10 @@ __global__ void __launch_bounds__(256) k_jacobi(Blocks B, const double* __restri
   double* Vb = V + (int64_t)b * LPAD * LPAD;
   for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
     const int i = q / LPAD, r = q % LPAD;  // Vb[i, r] = W[i, order[r]]
-    Vb[q] = (r < lb && i < lb) ? (double)W[i * LPAD + order[r]] : 0.0;
+    Vb[q] = (r < lb && i < lb) ? (double)W[i * LS + order[r]] : 0.0;
   }
   for (int r = threadIdx.x; r < LPAD; r += blockDim.x)
-    evals[(int64_t)b * LPAD + r] = r < lb ? (double)A[order[r] * LPAD + order[r]] : 0.0;
+    evals[(int64_t)b * LPAD + r] = r < lb ? (double)A[order[r] * LS + order[r]] : 0.0;
 }
 
 // Ritz vectors: Qout[v0 + i, r] = sum_j S[i, j] V[j, r] for r < kb (row panel S with
