@@ -270,7 +270,7 @@ template <class T, class TB, int LP>
 hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool write_st) {
   const int nb = w.B.nb;
   const int nu = (int)w.unit_block.size();
-  const size_t chol_smem = 2 * sizeof(double) * LP * LP;
+  const size_t chol_smem = 2 * sizeof(double) * LP * (LP + 1);
   HGL_TRY(set_smem(rsvd::k_chol_inv<LP>, chol_smem));
   const size_t ap_smem = sizeof(T) * (LP * LP + 128 * (LP + 1));
   HGL_TRY(set_smem(rsvd::k_apply_rinv<T, TB, LP>, ap_smem));

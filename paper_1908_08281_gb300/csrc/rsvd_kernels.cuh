@@ -408,9 +408,28 @@ k_block_gemm_f64(Blocks B, const int32_t* __restrict__ unit_block, const int32_t
 // writes a partial Gram; k_gram_reduce adds a block's partials in range order.  A
 // thread owns a TxT tile of the Gram (T = lpad/16): per row it reads T values of each
 // panel from shared memory and does T*T FMAs in the panel type; tile sums over 64 rows
-// are added into FP64 accumulators.
+// are added into accumulators of ~FP64 accuracy: FP64 for FP64 panels, an unevaluated
+// FP32 pair (TwoSum, Knuth) for FP32 panels -- FP64 adds and conversions would keep
+// the slow FP64 pipe the bound.
 // ---------------------------------------------------------------------------
 constexpr int GRAM_SPLIT = 1024;
+
+template <class T> struct GramAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T x) { s += (double)x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct GramAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 template <class T, int LPAD>
 __global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, const T* __restrict__ X,
@@ -427,11 +446,7 @@ __global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, con
   if (r_begin >= rows) return;
   const int r_end = rows < r_begin + GRAM_SPLIT ? rows : r_begin + GRAM_SPLIT;
   const int64_t r0 = B.arow[b];
-  double acc[TT][TT];
-#pragma unroll
-  for (int a = 0; a < TT; ++a)
-#pragma unroll
-    for (int c = 0; c < TT; ++c) acc[a][c] = 0.0;
+  GramAcc<T> acc[TT][TT];
   for (int t0 = r_begin; t0 < r_end; t0 += TR) {
     const int nr = r_end - t0 < TR ? r_end - t0 : TR;
     for (int q = threadIdx.x; q < TR * LPAD; q += blockDim.x) {
@@ -460,13 +475,13 @@ __global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, con
 #pragma unroll
     for (int a = 0; a < TT; ++a)
 #pragma unroll
-      for (int c = 0; c < TT; ++c) acc[a][c] += (double)part[a][c];
+      for (int c = 0; c < TT; ++c) acc[a][c].add(part[a][c]);
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < TT; ++a)
 #pragma unroll
-    for (int c = 0; c < TT; ++c) out[(ty + 16 * a) * LPAD + tx + 16 * c] = acc[a][c];
+    for (int c = 0; c < TT; ++c) out[(ty + 16 * a) * LPAD + tx + 16 * c] = acc[a][c].value();
 }
 
 // G[b] = sum of the block's partial Grams in range order
@@ -493,27 +508,32 @@ __global__ void k_gram_reduce(Blocks B, int max_splits, const double* __restrict
 template <int LPAD>
 __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __restrict__ G, double shift, double drop,
                                                    double* __restrict__ Rinv, int32_t* __restrict__ fail) {
+  // row stride LS = LPAD + 1 (odd): a warp walking down a column of doubles touches
+  // distinct banks
+  constexpr int LS = LPAD + 1;
   extern __shared__ double sm[];
-  double* L = sm;                   // LPAD x LPAD
-  double* X = sm + LPAD * LPAD;     // LPAD x LPAD
+  double* L = sm;                 // LPAD x LS
+  double* X = sm + LPAD * LS;     // LPAD x LS
   __shared__ double s_trace, s_dmax;
   __shared__ int dead[LPAD];
   __shared__ int s_ndead;
   const int b = blockIdx.x;
   const int lb = B.lb[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = 256 / 32;
   const double* Gb = G + (int64_t)b * LPAD * LPAD;
-  for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
-    const int i = q / LPAD, j = q % LPAD;
-    L[q] = (i < lb && j < lb) ? 0.5 * (Gb[i * LPAD + j] + Gb[j * LPAD + i]) : 0.0;
-    X[q] = 0.0;
-  }
+  for (int i = warp; i < LPAD; i += NW)
+    for (int j = lane; j < LPAD; j += 32) {
+      L[i * LS + j] = (i < lb && j < lb) ? 0.5 * (Gb[i * LPAD + j] + Gb[j * LPAD + i]) : 0.0;
+      X[i * LS + j] = 0.0;
+    }
   for (int j = threadIdx.x; j < LPAD; j += blockDim.x) dead[j] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     double tr = 0.0, dm = 0.0;
     for (int i = 0; i < lb; ++i) {
-      tr += L[i * LPAD + i];
-      dm = fmax(dm, L[i * LPAD + i]);
+      tr += L[i * LS + i];
+      dm = fmax(dm, L[i * LS + i]);
     }
     s_trace = tr;
     s_dmax = dm;
@@ -528,48 +548,47 @@ __global__ void __launch_bounds__(256) k_chol_inv(Blocks B, const double* __rest
   }
   const double sigma = shift * tr / lb;
   const double floor_pivot = drop * s_dmax;
-  for (int i = threadIdx.x; i < lb; i += blockDim.x) L[i * LPAD + i] += sigma;
+  for (int i = threadIdx.x; i < lb; i += blockDim.x) L[i * LS + i] += sigma;
   __syncthreads();
   // right-looking Cholesky with dropped pivots
   for (int j = 0; j < lb; ++j) {
     if (threadIdx.x == 0) {
-      const double d = L[j * LPAD + j];
+      const double d = L[j * LS + j];
       if (!(d > floor_pivot) || !isfinite(d)) {
         dead[j] = 1;
         s_ndead += 1;
-        L[j * LPAD + j] = 1.0;
+        L[j * LS + j] = 1.0;
       } else {
-        L[j * LPAD + j] = sqrt(d);
+        L[j * LS + j] = sqrt(d);
       }
     }
     __syncthreads();
-    const double dj = L[j * LPAD + j];
+    const double dj = L[j * LS + j];
     const bool dj_dead = dead[j] != 0;
     for (int i = j + 1 + threadIdx.x; i < lb; i += blockDim.x)
-      L[i * LPAD + j] = dj_dead ? 0.0 : L[i * LPAD + j] / dj;
+      L[i * LS + j] = dj_dead ? 0.0 : L[i * LS + j] / dj;
     __syncthreads();
-    const int m = lb - j - 1;
-    for (int q = threadIdx.x; q < m * m; q += blockDim.x) {
-      const int i = j + 1 + q / m, k = j + 1 + q % m;
-      if (k <= i) L[i * LPAD + k] -= L[i * LPAD + j] * L[k * LPAD + j];
+    // trailing update of the lower triangle: a warp per row, lanes along it
+    for (int i = j + 1 + warp; i < lb; i += NW) {
+      const double lij = L[i * LS + j];
+      for (int k = j + 1 + lane; k <= i; k += 32) L[i * LS + k] -= lij * L[k * LS + j];
     }
     __syncthreads();
   }
   // X = L^-1 (lower), one column per thread: forward substitution
   for (int c = threadIdx.x; c < lb; c += blockDim.x) {
-    X[c * LPAD + c] = 1.0 / L[c * LPAD + c];
+    X[c * LS + c] = 1.0 / L[c * LS + c];
     for (int i = c + 1; i < lb; ++i) {
       double sacc = 0.0;
-      for (int k = c; k < i; ++k) sacc += L[i * LPAD + k] * X[k * LPAD + c];
-      X[i * LPAD + c] = -sacc / L[i * LPAD + i];
+      for (int k = c; k < i; ++k) sacc += L[i * LS + k] * X[k * LS + c];
+      X[i * LS + c] = -sacc / L[i * LS + i];
     }
   }
   __syncthreads();
   // Rinv = X^T (upper); dead directions get a zero row and column
-  for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
-    const int i = q / LPAD, j = q % LPAD;
-    Rb[q] = (i < lb && j < lb && !dead[i] && !dead[j]) ? X[j * LPAD + i] : 0.0;
-  }
+  for (int i = warp; i < LPAD; i += NW)
+    for (int j = lane; j < LPAD; j += 32)
+      Rb[i * LPAD + j] = (i < lb && j < lb && !dead[i] && !dead[j]) ? X[j * LS + i] : 0.0;
   if (threadIdx.x == 0 && s_ndead) atomicAdd(fail, 1);
 }
 
