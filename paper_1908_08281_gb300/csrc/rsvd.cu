@@ -541,14 +541,14 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
     });
   } else if (bf16) {
     hgl::count_launch(2);
-    rsvd::k_assemble<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
-                                                            g->csc_idx, g->s, g->t,
-                                                            static_cast<__nv_bfloat16*>(wk.A));
+    rsvd::k_assemble<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
+        wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->s32, g->t32,
+        static_cast<__nv_bfloat16*>(wk.A));
     rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, seed_dev,
                                                          static_cast<__nv_bfloat16*>(wk.St));
   } else {
     hgl::count_launch(2);
-    rsvd::k_assemble<double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
+    rsvd::k_assemble<double, double><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr,
                                                      g->csc_idx, g->s, g->t, static_cast<double*>(wk.A));
     rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, seed_dev, static_cast<double*>(wk.St));
   }

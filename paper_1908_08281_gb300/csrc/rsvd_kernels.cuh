@@ -56,18 +56,30 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(
 template <class T> __device__ __forceinline__ double to_double(T x) { return (double)to_float<T>(x); }
 template <> __device__ __forceinline__ double to_double<double>(double x) { return x; }
 
+// storage <-> accumulation type of the block assembly (no FP64 step for FP32 sums)
+template <class TA> __device__ __forceinline__ TA from_acc(double x) { return from_double<TA>(x); }
+template <class TA> __device__ __forceinline__ TA from_acc(float x);
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <class TA, class S> __device__ __forceinline__ S to_acc(TA x) { return (S)to_float<TA>(x); }
+template <> __device__ __forceinline__ double to_acc<double, double>(double x) { return x; }
+
 // ---------------------------------------------------------------------------
 // Dense diagonal blocks Theta_bb[i, j] = s_u s_v sum_{e containing u and v} t_e,
 // u = v0 + i, v = v0 + j.  One warp per storage row: the row (padded width) is zeroed,
 // the diagonal is summed over the vertex's hyperedges, and the off-diagonal terms are
 // added hyperedge by hyperedge from the members that fall inside the block (found by
-// binary search in the sorted member list).  Padding rows stay zero.
+// binary search in the sorted member list).  Padding rows stay zero.  The sums run in
+// the scalings' type S: FP64 for FP64 blocks; FP32 (the graph's FP32 copies of s and t)
+// for BF16 blocks, whose 8-bit mantissa FP32 sums of ~20 terms carry exactly -- FP64
+// arithmetic and conversions kept the slow FP64 pipe 73% busy.
 // ---------------------------------------------------------------------------
-template <class TA>
+template <class TA, class S>
 __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict__ csr_ptr,
                            const int32_t* __restrict__ csr_idx, const int64_t* __restrict__ csc_ptr,
-                           const int32_t* __restrict__ csc_idx, const double* __restrict__ s,
-                           const double* __restrict__ t, TA* __restrict__ A) {
+                           const int32_t* __restrict__ csc_idx, const S* __restrict__ s,
+                           const S* __restrict__ t, TA* __restrict__ A) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -88,13 +100,13 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
     __syncwarp();
     const int64_t v0 = B.v0[b];
     const int64_t u = v0 + i;
-    const double su = s[u];
+    const S su = s[u];
     const int64_t beg = csr_ptr[u], end = csr_ptr[u + 1];
-    double d = 0.0;
+    S d = S(0);
     for (int64_t q = beg + lane; q < end; q += 32) d += t[csr_idx[q]];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-    if (lane == 0) row[i] = from_double<TA>(su * su * d);
+    if (lane == 0) row[i] = from_acc<TA>(su * su * d);
     __syncwarp();
     // off-diagonal terms: the lanes take 32 of u's hyperedges at a time and each finds
     // the members of its hyperedge inside [v0, v0 + bs) by two binary searches over
@@ -127,12 +139,12 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
         const int64_t l2 = __shfl_sync(0xffffffffu, lo, src);
         const int64_t h2 = __shfl_sync(0xffffffffu, hi, src);
         const int32_t e2 = __shfl_sync(0xffffffffu, e, src);
-        const double f = su * t[e2];
+        const S f = su * t[e2];
         for (int64_t p = l2 + lane; p < h2; p += 32) {
           const int32_t v = csc_idx[p];
           if (v != u) {
             const int64_t j = v - v0;
-            row[j] = from_double<TA>(to_double<TA>(row[j]) + f * s[v]);
+            row[j] = from_acc<TA>(to_acc<TA, S>(row[j]) + f * s[v]);
           }
         }
         __syncwarp();
