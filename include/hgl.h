@@ -95,6 +95,17 @@ uint64_t hgl_launch_count(void);
 hgl_status hgl_profile_enable(int32_t on);
 hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches);
 
+/*
+ * hgl_selftest_wait_timeout -- failure detection without a GPU fault: runs the bounded
+ * device wait that every tcgen05 kernel uses (an mbarrier poll that gives up after a
+ * cycle limit, records the error in a device status word and returns) on a barrier
+ * that nothing arrives on, with a limit of limit_cycles SM cycles (1 .. 8e9; the
+ * kernels' own limit is 4e9, about 2 s).  Returns HGL_ERR_TIMEOUT, the status a kernel
+ * reports when one of its waits runs out; the device stays usable.  Synchronises
+ * `stream`.
+ */
+hgl_status hgl_selftest_wait_timeout(int64_t limit_cycles, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Incidence (Section 2: H(v,e) = 1 iff v in e; de(e) = sum_v H(v,e))         */
 /* ------------------------------------------------------------------------- */

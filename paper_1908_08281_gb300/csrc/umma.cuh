@@ -69,19 +69,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // the caller can leave its loop.  The error word and the clock are read only every 64
 // polls (each poll is a try_wait, which itself suspends for a while): a global read on
 // every poll would delay the waiter's wake-up by a memory latency.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t* bar, uint32_t parity, int* err,
+                                                unsigned long long limit_cycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63u) == 0) {
       if (*(volatile int*)err != 0) return false;
-      if (clock64() - t0 > SPIN_CYCLES) {
+      if (clock64() - t0 > limit_cycles) {
         atomicExch(err, 1);
         return false;
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  return mbar_wait_limit(bar, parity, err, SPIN_CYCLES);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {

@@ -293,8 +293,15 @@ k_cg_reduce(const double* __restrict__ pa, const double* __restrict__ pb, int ro
         }
       } else if (MODE == RED_RESID) {
         S.rr[j] = a;
-        S.relres[j] = S.b2[j] > 0.0 ? sqrt(a / S.b2[j]) : 0.0;
-        if (!isfinite(a)) S.bad[j] = 1;
+        const double b2 = S.b2[j];
+        if (!isfinite(a) || !isfinite(b2)) {
+          // a non-finite right-hand side or residual: relres NaN, so the column is
+          // reported non-finite instead of passing as relres 0
+          S.bad[j] = 1;
+          S.relres[j] = __longlong_as_double(0x7ff8000000000000LL);
+        } else {
+          S.relres[j] = b2 > 0.0 ? sqrt(a / b2) : 0.0;
+        }
       }
     }
   }

@@ -90,6 +90,7 @@ _SIGNATURES = {
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_precond_tensor_cores": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "hgl_set_block_product": (_I32, [_P, _I32]),
+    "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
@@ -340,7 +341,7 @@ def cg_solve(g: Graph, w: torch.Tensor, lam: float, Y: torch.Tensor, F: torch.Te
                             precond.handle if precond is not None else None, ctypes.byref(opts),
                             ctypes.c_void_p(relres.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
                             ctypes.byref(stats), _stream(stream))
-    if st != 0 and (raise_on_fail or st not in (-7,)):
+    if st != 0 and (raise_on_fail or st not in (-7, -9)):
         _check(st)
     return F, relres, iters, stats
 
@@ -373,6 +374,12 @@ def precond_apply(P: Precond, R: torch.Tensor, Z: torch.Tensor | None = None, st
     pz, ldz, _ = _panel(Z, "Z")
     _check(lib().hgl_precond_apply(P.handle, pr, ldr, pz, ldz, c, dt, _stream(stream)))
     return Z
+
+
+def selftest_wait_timeout(limit_cycles: int, stream=None):
+    """Run the kernels' bounded device wait against a barrier nothing arrives on; raises
+    HglError with status HGL_ERR_TIMEOUT (the expected outcome)."""
+    _check(lib().hgl_selftest_wait_timeout(int(limit_cycles), _stream(stream)))
 
 
 def set_block_product(g: Graph, mode: int):

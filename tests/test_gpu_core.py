@@ -257,6 +257,38 @@ def test_cg_zero_column_warm_start_and_ragged_c():
     assert _relcol(F2.cpu().numpy(), ref).max() <= 1e-10
 
 
+def test_device_wait_timeout_reports_status_and_device_stays_usable():
+    """A bounded device wait on a barrier that nothing arrives on gives up after its
+    cycle limit and the call returns HGL_ERR_TIMEOUT; the next launches run normally."""
+    for limit in (1000, 2_000_000):
+        with pytest.raises(hgl.HglError) as ei:
+            hgl.selftest_wait_timeout(limit)
+        assert ei.value.status == -8
+    wl, d, og, H = _case("small_fp64", 11, n=300, m=450, c=3)
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    w = np.full(d["m"], 1.0 / d["m"])
+    Z = hgl.apply_theta(g, torch.tensor(w, device=DEV), _panel(d["Y"]), 1.5, -1.0).cpu().numpy()
+    assert np.allclose(Z, core.theta_apply(H, w, d["Y"], 1.5, -1.0), rtol=1e-12, atol=1e-14)
+
+
+def test_nonfinite_right_hand_side_reports_status():
+    """A NaN in one column of Y: that column is reported non-finite (HGL_ERR_NONFINITE),
+    the others still converge to the oracle's solution."""
+    wl, d, og, H = _case("small_fp64", 12, n=500, m=800, c=4)
+    w = np.full(d["m"], 1.0 / d["m"])
+    Yn = d["Y"].copy()
+    Yn[7, 1] = np.nan
+    g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+    for mode in (hgl.HGL_FP64, hgl.HGL_FP32):
+        F, relres, iters, st = hgl.cg_solve(g, torch.tensor(w, device=DEV), 1.0, _panel(Yn), tol=1e-8, dtype=mode,
+                                            raise_on_fail=False)
+        assert st.status == -9, (mode, st.status)
+        ref = core.solve_dense(H, w, 1.0, d["Y"])
+        ok = [0, 2, 3]
+        err = _relcol(F.cpu().numpy()[:, ok], ref[:, ok])
+        assert err.max() <= 2 * 1e-8 * 1.01, (mode, err.max())
+
+
 def test_cg_not_converged_status():
     wl, d, og, H = _case("small_fp64", 5, n=400, m=600, c=3)
     g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
