@@ -14,7 +14,8 @@ Readings of points the paper leaves open (each also listed in the design notes):
     projection of w - eta * grad P onto {w >= 0, 1^T w = 1} (sort and threshold).
   * "Block" CG is one independent CG per right-hand-side column (Eqs. 16-20 applied
     column by column); the stopping test is ||r_j|| <= tol * ||lam y_j|| on the
-    recursively updated residual.
+    recursively updated residual.  O'Leary's shared-Krylov block CG is provided
+    beside it (``block_cg_solve``) for groups of columns.
 """
 from __future__ import annotations
 
@@ -195,6 +196,72 @@ def cg_solve(H: sp.spmatrix, w: np.ndarray, lam: float, Y: np.ndarray, F0=None,
         "true_relres": np.sqrt((true_r * true_r).sum(axis=0)) / safe,
         "history": hist,
     }
+
+
+def block_cg_solve(H: sp.spmatrix, w: np.ndarray, lam: float, Y: np.ndarray, s: int, F0=None,
+                   tol: float = 1e-10, max_iter: int = 1000, precond=None, rank_tol: float = 1e-12):
+    """Block CG with a shared Krylov space (O'Leary, "The block conjugate gradient
+    algorithm and related methods", Linear Algebra Appl. 29, 1980) on M F = lam Y, the
+    columns taken in groups of s.  Each group runs the block recurrences with the search
+    block kept orthonormal and rank revealed, the breakdown-free form of Ji and Li
+    (2017), so that columns that converge or become dependent leave the search space
+    instead of making P^T M P singular:
+
+        R_0 = B - M F_0,  Z_0 = P^-1 R_0,  P_0 = orth(Z_0)
+        repeat:  Q = M P;  a = (P^T Q)^-1 P^T R;  F += P a;  R -= Q a
+                 stop when ||r_j|| <= tol ||b_j|| for every column of the group
+                 Z = P^-1 R;  b = -(P^T Q)^-1 Q^T Z;  P = orth(Z + P b)
+
+    orth(.) is an orthonormal basis of the range from the SVD, dropping singular values
+    below rank_tol times the largest (so P can have fewer than s columns).  With s = 1
+    this is per-column CG up to the normalisation of p.  Returns dict(F, iters[groups],
+    group_of[c], relres[c] (recursive), true_relres[c]).
+    """
+    Y = np.asarray(Y, dtype=np.float64)
+    n, c = Y.shape
+    B = lam * Y
+    F = np.zeros((n, c)) if F0 is None else np.array(F0, dtype=np.float64)
+    bnorm = np.sqrt((B * B).sum(axis=0))
+    safe = np.where(bnorm > 0, bnorm, 1.0)
+    relres = np.zeros(c)
+    groups = [list(range(g0, min(g0 + s, c))) for g0 in range(0, c, s)]
+    iters = np.zeros(len(groups), dtype=np.int64)
+    group_of = np.zeros(c, dtype=np.int64)
+
+    def orth(A):
+        if A.shape[1] == 0:
+            return A
+        U, sv, _ = np.linalg.svd(A, full_matrices=False)
+        if sv.size == 0 or sv[0] == 0.0:
+            return A[:, :0]
+        return U[:, sv > rank_tol * sv[0]]
+
+    for gi, cols in enumerate(groups):
+        group_of[cols] = gi
+        R = B[:, cols] - theta_apply(H, w, F[:, cols], 1.0 + lam, -1.0)
+        Fg = F[:, cols].copy()
+        conv = lambda R_: bool((np.sqrt((R_ * R_).sum(axis=0)) <= tol * bnorm[cols]).all())
+        if not conv(R):
+            P = orth(R if precond is None else precond(R))
+            for _ in range(max_iter):
+                if P.shape[1] == 0:
+                    break
+                Q = theta_apply(H, w, P, 1.0 + lam, -1.0)
+                PQ = P.T @ Q
+                a = np.linalg.solve(PQ, P.T @ R)
+                Fg = Fg + P @ a
+                R = R - Q @ a
+                iters[gi] += 1
+                if conv(R):
+                    break
+                Z = R if precond is None else precond(R)
+                b = -np.linalg.solve(PQ, Q.T @ Z)
+                P = orth(Z + P @ b)
+        F[:, cols] = Fg
+        relres[cols] = np.sqrt((R * R).sum(axis=0)) / safe[cols]
+    true_r = B - theta_apply(H, w, F, 1.0 + lam, -1.0)
+    return {"F": F, "iters": iters, "group_of": group_of, "relres": relres,
+            "true_relres": np.sqrt((true_r * true_r).sum(axis=0)) / safe}
 
 
 def cg_iteration_bound(lam: float, tol: float) -> int:

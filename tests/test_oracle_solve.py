@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import synth
-from oracle.core import (certified_solve, cg_iteration_bound, cg_solve, solve_dense,
+from oracle.core import (block_cg_solve, certified_solve, cg_iteration_bound, cg_solve, solve_dense,
                          system_dense, theta_apply, theta_dense)
 from oracle.incidence import build_incidence, incidence_matrix
 
@@ -104,3 +104,83 @@ def test_iteration_bound_values():
     # kappa = 2 at lam = 1 and 3 at lam = 0.5
     assert cg_iteration_bound(1.0, 1e-10) == 14
     assert cg_iteration_bound(0.5, 1e-8) == 15
+
+
+# ---------------------------------------------------------------- block CG ---
+
+def _spd_case(n=24, m=40, c=6, seed=3):
+    """A small hypergraph whose M has well-spread eigenvalues (random sizes 2..6)."""
+    rng = np.random.default_rng(seed)
+    ptr, mem = [0], []
+    for _ in range(m):
+        k = int(rng.integers(2, 7))
+        mem.extend(sorted(rng.choice(n, k, replace=False)))
+        ptr.append(len(mem))
+    H = incidence_matrix(build_incidence(n, m, np.asarray(ptr, np.int64), np.asarray(mem, np.int32)))
+    w = rng.random(m) + 0.1
+    w /= w.sum()
+    Y = rng.standard_normal((n, c))
+    return H, w, Y
+
+
+def test_block_cg_matches_dense(small):
+    """Block CG in groups of 4 (a ragged last group of 2) reaches the dense solution."""
+    H, w, Y, lam = small
+    Fd = solve_dense(H, w, lam, Y)
+    out = block_cg_solve(H, w, lam, Y, s=4, tol=1e-12)
+    err = np.linalg.norm(out["F"] - Fd, axis=0) / np.linalg.norm(Fd, axis=0)
+    assert err.max() < 1e-10
+    assert out["true_relres"].max() < 1e-11
+    assert list(out["group_of"]) == [0, 0, 0, 0, 1, 1, 1, 1, 2, 2]
+
+
+def test_block_cg_finite_termination():
+    """In exact arithmetic the shared Krylov space grows by s dimensions per iteration,
+    so s columns finish within ceil(n/s) iterations (here n = 24, s = 6: at most 4, plus
+    one for rounding), where per-column CG needs up to n."""
+    H, w, Y = _spd_case()
+    lam = 0.05  # kappa(M) up to 21: per-column CG needs many iterations
+    out = block_cg_solve(H, w, lam, Y, s=6, tol=1e-11)
+    assert out["true_relres"].max() < 1e-10
+    assert out["iters"].max() <= 24 // 6 + 1, out["iters"]
+    per_col = cg_solve(H, w, lam, Y, tol=1e-11)
+    assert per_col["iters"].max() > out["iters"].max()
+
+
+def test_block_cg_s1_is_per_column_cg(small):
+    """With s = 1 the block recurrences are CG's, up to the normalisation of p: the same
+    iteration count and solution."""
+    H, w, Y, lam = small
+    a = block_cg_solve(H, w, lam, Y, s=1, tol=1e-10)
+    b = cg_solve(H, w, lam, Y, tol=1e-10)
+    assert np.array_equal(a["iters"], b["iters"])
+    assert np.abs(a["F"] - b["F"]).max() < 1e-10 * np.abs(b["F"]).max()
+
+
+def test_block_cg_dependent_and_zero_columns():
+    """A repeated column and a zero column in one group: the rank-revealing search block
+    drops the dependent directions instead of breaking down; the repeated columns get
+    equal solutions and the zero column stays zero."""
+    H, w, Y = _spd_case(seed=4)
+    Y[:, 2] = Y[:, 0]
+    Y[:, 3] = 0.0
+    lam = 0.3
+    out = block_cg_solve(H, w, lam, Y, s=6, tol=1e-12)
+    Fd = solve_dense(H, w, lam, Y)
+    assert np.abs(out["F"] - Fd).max() < 1e-10 * np.abs(Fd).max()
+    assert np.abs(out["F"][:, 2] - out["F"][:, 0]).max() < 1e-10 * np.abs(Fd).max()
+    assert np.abs(out["F"][:, 3]).max() == 0.0
+
+
+def test_block_cg_preconditioned_and_warm_start(small):
+    """With a Jacobi-like SPD preconditioner and a warm start from a nearby F, block CG
+    still reaches the dense solution, in fewer iterations than from zero."""
+    H, w, Y, lam = small
+    Fd = solve_dense(H, w, lam, Y)
+    d = np.diag(system_dense(H, w, lam))
+    pre = lambda R: R / d[:, None]
+    cold = block_cg_solve(H, w, lam, Y, s=5, tol=1e-12, precond=pre)
+    warm = block_cg_solve(H, w, lam, Y, s=5, tol=1e-12, precond=pre, F0=Fd * (1 + 1e-6))
+    for out in (cold, warm):
+        assert np.abs(out["F"] - Fd).max() < 1e-10 * np.abs(Fd).max()
+    assert warm["iters"].max() < cold["iters"].max()
