@@ -734,12 +734,10 @@ hgl_status tc_apply(hgl_precond* P, const float* R, int64_t ldr, float* Z, int64
   HGL_TRY(encode_map_2d(&mCl, f32, Cl, KP, (uint64_t)P->nb * c128, KP * 4, 32, EX_COLS, CU_TENSOR_MAP_SWIZZLE_128B));
   const size_t smem_pj = pj_smem_bytes<KP>();
   const size_t smem_ex = ex_smem_bytes<KP>();
-  static bool attr_set = false;
-  if (!attr_set) {
-    HGL_TRY(tc_smem_attr(k_pc_proj_tc<KP>, smem_pj));
-    HGL_TRY(tc_smem_attr(k_pc_expand_tc<KP>, smem_ex));
-    attr_set = true;
-  }
+  // per call (a host-side attribute, also valid while a stream is being captured): the
+  // setting is per device, and a process may apply on several
+  HGL_TRY(tc_smem_attr(k_pc_proj_tc<KP>, smem_pj));
+  HGL_TRY(tc_smem_attr(k_pc_expand_tc<KP>, smem_ex));
   const int sms = device_sm_count();
   PjArgs pa{P->blk_order, P->d_v0, P->d_rows, P->nb, (int)(c128 / PJ_COLS), c, P->k, P->gain32,
             1.0 / (1.0 + P->lam), Ch, Cl, c128, rz, run_flag, P->d_err};
