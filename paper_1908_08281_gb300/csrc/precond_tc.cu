@@ -174,7 +174,8 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
   uint64_t* a_empty = a_full + PJ_ASTAGES;
   uint64_t* acc_full = a_empty + PJ_ASTAGES;  // 2
   uint64_t* acc_empty = acc_full + 2;           // 2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_drain = acc_empty + 2;          // 1: the issuer's MMAs, after an error
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_drain + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -197,6 +198,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, 4);
     }
+    mbar_init(mma_drain, 1);
     umma::fence_barrier_init();
   }
   if (warp == 2) umma::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -228,6 +230,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      umma::ArmedPhases<(PJ_RSTAGES > PJ_BSTAGES ? PJ_RSTAGES : PJ_BSTAGES)> armed;
       for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         int b, ct, nsteps;
         int64_t b0, bend, rs;
@@ -237,6 +240,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
             ok = false;
             break;
           }
+          armed.p[stage] = (uint8_t)phase;
           const int row = (int)(rs + (int64_t)s * PJ_ROWS);
           if (rprod) {
             mbar_arrive_expect_tx(full + stage, PJ_R_BYTES);
@@ -253,6 +257,7 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
           }
         }
       }
+      if (*(volatile int*)a.err != 0) armed.drain(full);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -303,6 +308,10 @@ k_pc_proj_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ C
           acc = 0;
           acc_phase ^= 1;
         }
+      }
+      if (*(volatile int*)a.err != 0) {
+        umma::mma_commit(mma_drain);
+        umma::mbar_drain(mma_drain, 0);
       }
     }
   } else if (warp >= 4) {
@@ -471,7 +480,8 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
   uint64_t* r_empty = r_full + EX_RSTAGES;
   uint64_t* acc_full = r_empty + EX_RSTAGES;  // 2
   uint64_t* acc_empty = acc_full + 2;         // 2
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_drain = acc_empty + 2;        // 1: the issuer's MMAs, after an error
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_drain + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -491,6 +501,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, 4);
     }
+    mbar_init(mma_drain, 1);
     umma::fence_barrier_init();
   }
   if (warp == 2) umma::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -505,10 +516,13 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
       int stage = 0;
       uint32_t phase = 0, aphase = 0;
       bool ok = true;
+      umma::ArmedPhases<EX_BSTAGES> armed;
+      umma::ArmedPhases<1> a_armed;
       for (int u = blockIdx.x; u < a.nexp && ok; u += gridDim.x) {
         const int b = a.exp_block[u];
         const int row0 = (int)(a.v0[b] + (int64_t)a.exp_tile[u] * EX_ROWS);
         if (!mbar_wait(a_empty, aphase ^ 1, a.err)) break;
+        a_armed.p[0] = (uint8_t)aphase;  // the phase of a_full this load completes
         aphase ^= 1;
         mbar_arrive_expect_tx(a_full, A_BYTES);
 #pragma unroll
@@ -522,6 +536,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
             ok = false;
             break;
           }
+          armed.p[stage] = (uint8_t)phase;
           uint8_t* sb = sB + stage * B_BYTES;
           mbar_arrive_expect_tx(b_full + stage, B_BYTES);
 #pragma unroll
@@ -535,6 +550,10 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
           }
         }
       }
+      if (*(volatile int*)a.err != 0) {
+        armed.drain(b_full);
+        a_armed.drain(a_full);
+      }
     }
   } else if (warp == 3) {
     // ---------------- TMA producer: R tiles ----------------
@@ -542,6 +561,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      umma::ArmedPhases<EX_RSTAGES> armed;
       for (int u = blockIdx.x; u < a.nexp && ok; u += gridDim.x) {
         const int b = a.exp_block[u];
         const int row0 = (int)(a.v0[b] + (int64_t)a.exp_tile[u] * EX_ROWS);
@@ -550,6 +570,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
             ok = false;
             break;
           }
+          armed.p[stage] = (uint8_t)phase;
           uint8_t* sr = sR + stage * EX_R_BYTES;
           mbar_arrive_expect_tx(r_full + stage, EX_R_BYTES);
 #pragma unroll
@@ -561,6 +582,7 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
           }
         }
       }
+      if (*(volatile int*)a.err != 0) armed.drain(r_full);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -606,6 +628,10 @@ k_pc_expand_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__
           }
         }
         umma::mma_commit(a_empty);  // the Q tile is free once this unit's MMAs are done
+      }
+      if (*(volatile int*)a.err != 0) {
+        umma::mma_commit(mma_drain);
+        umma::mbar_drain(mma_drain, 0);
       }
     }
   } else if (warp >= 4) {

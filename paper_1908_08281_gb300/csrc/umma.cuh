@@ -89,6 +89,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return mbar_wait_limit(bar, parity, err, SPIN_CYCLES);
 }
 
+// After a role gave up: wait, again with a limit and whatever the error word says,
+// for phase `parity` of `bar` -- the landing of a copy this thread issued, or (with a
+// commit barrier) the completion of its MMAs -- so that nothing still writes shared
+// memory or reads TMEM when the CTA frees them and exits.
+constexpr unsigned long long DRAIN_CYCLES = 200000000ull;  // ~0.1 s
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > DRAIN_CYCLES) return;
+}
+
+// Per-stage record of the phase a producer last armed (2 = never), for the drain.
+template <int N>
+struct ArmedPhases {
+  uint8_t p[N];
+  __device__ __forceinline__ ArmedPhases() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = 2;
+  }
+  __device__ __forceinline__ void drain(uint64_t* full) const {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (p[i] != 2) mbar_drain(full + i, p[i]);
+  }
+};
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -239,7 +265,8 @@ k_block_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;   // 2
   uint64_t* acc_empty = acc_full + 2;    // 2
-  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* mma_drain = acc_empty + 2;   // 1: the issuer's MMAs, after an error
+  uint32_t* tmem_base_slot = reinterpret_cast<uint32_t*>(mma_drain + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -253,6 +280,7 @@ k_block_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       mbar_init(acc_full + b, 1);
       mbar_init(acc_empty + b, 4);  // one arrival per epilogue warp
     }
+    mbar_init(mma_drain, 1);
     fence_barrier_init();
   }
   if (warp == 2) tmem_alloc(tmem_base_slot, TMEM_COLS);
@@ -267,6 +295,7 @@ k_block_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      ArmedPhases<STAGES> armed;
       for (int u = blockIdx.x; u < U.nunits && ok; u += gridDim.x) {
         const int b = U.unit_block[u];
         const int tile = U.unit_tile[u];
@@ -283,12 +312,14 @@ k_block_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           mbar_arrive_expect_tx(full + stage, STAGE_BYTES);
           tma_load_2d(sa, &mapA, full + stage, kt * BLOCK_K, ay);
           tma_load_2d(sa + A_BYTES, &mapB, full + stage, bx0 + kt * BLOCK_K, 0);
+          armed.p[stage] = (uint8_t)phase;
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
+      if (*(volatile int*)err != 0) armed.drain(full);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -332,6 +363,10 @@ k_block_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           acc = 0;
           acc_phase ^= 1;
         }
+      }
+      if (*(volatile int*)err != 0) {
+        mma_commit(mma_drain);
+        mbar_drain(mma_drain, 0);
       }
     }
   } else if (warp >= 4) {
