@@ -271,6 +271,29 @@ hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double lam, const d
                         double* relres, int32_t* iters, hgl_solve_stats* stats,
                         void* stream);
 
+/*
+ * hgl_block_cg_solve -- M F = lam Y by block CG with a shared Krylov space (O'Leary 1980)
+ * over groups of s columns (the last group may be narrower), FP64: per group
+ *   R = lam Y - M F, P = orth(R); repeat Q = M P, a = (P^T Q)^+ P^T R, F += P a,
+ *   R -= Q a, stop when every column has ||r_j|| <= tol ||lam y_j||,
+ *   b = -(P^T Q)^+ Q^T R, P = orth(R + P b),
+ * with orth = CholeskyQR2 on unit-normalised columns and dropped pivots (the
+ * breakdown-free form of Ji and Li, 2017: converged or dependent directions leave the
+ * search block).  The groups share every launch; with s = 1 this is CG.
+ *   Y, F      device FP64 n x c, leading dimensions ldy, ldf; F is read as f_0 with
+ *             flags & HGL_SOLVE_WARM_START (else f_0 = 0) and holds the solution
+ *   s         columns per group, 1 .. 32
+ *   relres    optional device FP64[c]: the recomputed ||lam y_j - M f_j|| / ||lam y_j||
+ *   iters     optional device int32[ceil(c/s)]: iterations per group
+ * Allocates its work space (7 panels n x c and small per-group arrays) per call.
+ * Returns HGL_ERR_NOT_CONVERGED or HGL_ERR_NONFINITE as hgl_cg_solve does.
+ * Synchronises `stream`.
+ */
+hgl_status hgl_block_cg_solve(const hgl_graph* g, const double* w, double lam, const double* Y,
+                              int64_t ldy, double* F, int64_t ldf, int32_t c, int32_t s, double tol,
+                              int32_t max_iter, int32_t flags, double* relres, int32_t* iters,
+                              void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Block randomized SVD (Section 3, Algorithm 1) as a block preconditioner   */
 /* ------------------------------------------------------------------------- */

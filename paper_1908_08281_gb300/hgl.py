@@ -91,6 +91,7 @@ _SIGNATURES = {
     "hgl_precond_tensor_cores": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "hgl_set_block_product": (_I32, [_P, _I32]),
     "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
+    "hgl_block_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
@@ -344,6 +345,29 @@ def cg_solve(g: Graph, w: torch.Tensor, lam: float, Y: torch.Tensor, F: torch.Te
     if st != 0 and (raise_on_fail or st not in (-7, -9)):
         _check(st)
     return F, relres, iters, stats
+
+
+def block_cg_solve(g: Graph, w: torch.Tensor, lam: float, Y: torch.Tensor, s: int, F: torch.Tensor | None = None,
+                   tol: float = 1e-10, max_iter: int = 1000, warm_start: bool = False, stream=None,
+                   raise_on_fail: bool = True):
+    """Block CG with a shared Krylov space over groups of s columns (FP64); returns
+    (F, relres[c], iters[ceil(c/s)], status)."""
+    n, c = Y.shape
+    if F is None:
+        F = padded_panel(n, c, torch.float64, Y.device)
+    py, ldy, dty = _panel(Y, "Y")
+    pf, ldf, dtf = _panel(F, "F")
+    if dty != HGL_FP64 or dtf != HGL_FP64:
+        raise ValueError("Y and F must be float64")
+    relres = torch.empty(c, dtype=torch.float64, device=Y.device)
+    # one entry per group; an invalid s (rejected by the library) still gets a buffer
+    iters = torch.empty(max(1, (c + s - 1) // s) if s >= 1 else 1, dtype=torch.int32, device=Y.device)
+    st = lib().hgl_block_cg_solve(g.handle, _vec(w, "w"), lam, py, ldy, pf, ldf, c, s, tol, max_iter,
+                                  HGL_SOLVE_WARM_START if warm_start else 0, ctypes.c_void_p(relres.data_ptr()),
+                                  ctypes.c_void_p(iters.data_ptr()), _stream(stream))
+    if st != 0 and (raise_on_fail or st not in (-7, -9)):
+        _check(st)
+    return F, relres, iters, st
 
 
 def block_rsvd(g: Graph, w: torch.Tensor, lam: float, block_ptr, k: int, p: int, q: int, seed: int,
