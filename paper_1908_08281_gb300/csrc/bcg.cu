@@ -24,7 +24,11 @@ constexpr int BCG_MAXS = 32;
 constexpr int BCG_THREADS = 256;
 constexpr int GRAM_SLAB = 2048;   // rows per partial Gram
 constexpr int GRAM_TILE = 64;     // rows staged in shared memory at a time
-constexpr double PIVOT_DROP = 1e-12;  // relative pivot of a unit-diagonal Gram
+// Relative pivot of a unit-diagonal Gram below which a direction is dropped.  The Gram
+// squares the singular values of the block, so this drops directions whose singular
+// value is below 1e-6 of the column norms: the same rank decision as an SVD-based
+// orthonormalisation with a relative singular-value threshold of 1e-6.
+constexpr double PIVOT_DROP = 1e-12;
 
 struct DevBuf {
   void* p = nullptr;
@@ -335,9 +339,10 @@ extern "C" hgl_status hgl_block_cg_solve(const hgl_graph* gc, const double* w, d
   double* sqpart = gram + small;
   double* colsq = sqpart + (size_t)nsq * cp;
   int32_t* d_active = reinterpret_cast<int32_t*>(colsq + cp);
-  // search, product and scratch panels start at zero (a group that never becomes
-  // active keeps zero columns there)
-  HGL_CHECK_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * 5 * panel, st));
+  // all seven panels start at zero, padding columns (j >= cp) included: a group that
+  // never becomes active keeps zero columns in the search, product and scratch panels,
+  // and the operator's 16-byte loads read defined values in the padding
+  HGL_CHECK_CUDA(cudaMemsetAsync(Bp, 0, sizeof(double) * 7 * panel, st));
 
   const int vec_blocks = g->num_sms * 8;
   auto gram_of = [&](const double* A, const double* Bm, double* out) -> hgl_status {
@@ -418,6 +423,12 @@ extern "C" hgl_status hgl_block_cg_solve(const hgl_graph* gc, const double* w, d
                                          Bp, Fp, ldp);
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(col_norms(Bp, bnorm));
+  // a column with a zero right-hand side has the exact solution 0 (M is nonsingular):
+  // a warm start there is discarded, so the column starts (and stays) converged
+  if (flags & HGL_SOLVE_WARM_START)
+    for (int j = 0; j < c; ++j)
+      if (bnorm[j] == 0.0)
+        HGL_CHECK_CUDA(cudaMemset2DAsync(Fp + j, sizeof(double) * ldp, 0, sizeof(double), n, st));
   HGL_TRY(apply_m(Fp, Q));
   count_launch();
   k_bcg_sub<<<vec_blocks, 256, 0, st>>>(n, cp, Bp, Q, R, ldp);
@@ -457,7 +468,9 @@ extern "C" hgl_status hgl_block_cg_solve(const hgl_graph* gc, const double* w, d
   std::vector<double> rel(c);
   int missed = 0, nonfinite = 0;
   for (int j = 0; j < c; ++j) {
-    rel[j] = bnorm[j] > 0.0 ? hsq[j] / bnorm[j] : 0.0;
+    // relative residual; for a zero right-hand side the absolute ||r_j|| (0 after the
+    // column was zeroed, so such a column always meets the tolerance)
+    rel[j] = bnorm[j] > 0.0 ? hsq[j] / bnorm[j] : hsq[j];
     if (!std::isfinite(rel[j]) || !std::isfinite(bnorm[j])) nonfinite++;
     else if (rel[j] > tol) missed++;
   }

@@ -61,7 +61,9 @@ def test_block_cg_matches_oracle(s):
     tol = 1e-10
     F, relres, iters, st = hgl.block_cg_solve(g, torch.tensor(w, device=DEV), wl.lam, _panel(d["Y"]), s, tol=tol)
     assert st == 0
-    o = block_cg_solve(H, w, wl.lam, d["Y"], s=s, tol=tol)
+    # the GPU drops Gram pivots below 1e-12, i.e. singular values below 1e-6 (the Gram
+    # squares them): the oracle takes the same rank decision with rank_tol = 1e-6
+    o = block_cg_solve(H, w, wl.lam, d["Y"], s=s, tol=tol, rank_tol=1e-6)
     assert np.abs(iters.cpu().numpy().astype(int) - o["iters"]).max() <= 1, (iters, o["iters"])
     Fd = solve_dense(H, w, wl.lam, d["Y"])
     err = np.linalg.norm(F.cpu().numpy() - Fd, axis=0) / np.linalg.norm(Fd, axis=0)
@@ -100,10 +102,35 @@ def test_block_cg_dependent_zero_columns_and_warm_start():
     assert np.abs(Fg[:, 3]).max() == 0.0
     F0 = _panel(Fd * (1 + 1e-6))
     F2, _, iters2, st2 = hgl.block_cg_solve(g, wt, lam, _panel(Y), 6, F=F0, tol=1e-12, warm_start=True)
-    o = block_cg_solve(H, w, lam, Y, s=6, tol=1e-12, F0=Fd * (1 + 1e-6))
+    o = block_cg_solve(H, w, lam, Y, s=6, tol=1e-12, F0=Fd * (1 + 1e-6), rank_tol=1e-6)
     assert st2 == 0 and abs(int(iters2.cpu()[0]) - int(o["iters"][0])) <= 1
     assert int(iters2.cpu()[0]) <= int(iters.cpu()[0])
     assert np.abs(F2.cpu().numpy() - Fd).max() <= 1e-10 * np.abs(Fd).max()
+
+
+def test_block_cg_zero_column_with_nonzero_warm_start():
+    """A zero right-hand-side column has the exact solution 0: a nonzero warm start there
+    is discarded, the column comes back exactly 0 with relres 0, and the other columns
+    match the oracle's block CG run from the same warm start with that column zeroed
+    (what the solver starts from), in iterations and solution."""
+    H, g, w, Y = _spd_case(seed=7)
+    Y[:, 1] = 0.0
+    lam = 0.4
+    wt = torch.tensor(w, device=DEV)
+    Fd = solve_dense(H, w, lam, Y)
+    F0 = Fd * (1 + 1e-3)
+    F0[:, 1] = 1.0
+    F, relres, iters, st = hgl.block_cg_solve(g, wt, lam, _panel(Y), 6, F=_panel(F0), tol=1e-12, warm_start=True)
+    assert st == 0
+    Fg = F.cpu().numpy()
+    assert np.abs(Fg[:, 1]).max() == 0.0
+    assert float(relres.cpu()[1]) == 0.0
+    F0z = F0.copy()
+    F0z[:, 1] = 0.0
+    o = block_cg_solve(H, w, lam, Y, s=6, tol=1e-12, F0=F0z, rank_tol=1e-6)
+    assert abs(int(iters.cpu()[0]) - int(o["iters"][0])) <= 1, (iters, o["iters"])
+    assert np.abs(Fg - o["F"]).max() <= 1e-10 * np.abs(Fd).max()
+    assert np.abs(Fg - Fd).max() <= 1e-10 * np.abs(Fd).max()
 
 
 def test_block_cg_argument_errors():
