@@ -185,7 +185,10 @@ hgl_status hgl_apply_theta(const hgl_graph* g, const double* w, double a, double
  * m <= 1,048,576 for BF16 panels, else HGL_ERR_INVALID_ARG (nothing launched).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current and caches it; make that first
- * call before any stream capture.  All calls share the one array and it keeps the
+ * call before any stream capture.  The cached address belongs to the device's
+ * context: after cudaDeviceReset the next call would use a stale address, so a
+ * program that resets a device must not call this entry point on it again.  All
+ * calls share the one array and it keeps the
  * last call's contents; it needs no clearing, since the hyperedge pass writes every
  * entry that the vertex pass then reads.  Calls that overlap on the GPU (on
  * different streams, or from different host threads) race on the array and give
@@ -279,7 +282,10 @@ hgl_status hgl_cg_solve(const hgl_graph* g, const double* w, double lam, const d
  *   b = -(P^T Q)^+ Q^T R, P = orth(R + P b),
  * with orth = CholeskyQR2 on unit-normalised columns and dropped pivots (the
  * breakdown-free form of Ji and Li, 2017: converged or dependent directions leave the
- * search block).  The groups share every launch; with s = 1 this is CG.
+ * search block).  A pivot of the unit-diagonal Gram below 1e-12 drops its direction,
+ * i.e. singular values below 1e-6 of the column norms (the Gram squares them).  The
+ * groups share every launch; with s = 1 this is CG.  A zero column of Y gives F_j = 0
+ * (a warm start in that column is discarded) and reports relres_j = ||r_j|| = 0.
  *   Y, F      device FP64 n x c, leading dimensions ldy, ldf; F is read as f_0 with
  *             flags & HGL_SOLVE_WARM_START (else f_0 = 0) and holds the solution
  *   s         columns per group, 1 .. 32
@@ -448,6 +454,21 @@ hgl_status hgl_adjoint_grad(hgl_graph* g, const double* w, double lam, const dou
                             const double* G, double* Z, int64_t ld, int32_t c,
                             const hgl_precond* precond, const hgl_solve_opts* opts,
                             double* grad, hgl_solve_stats* stats, void* stream);
+
+/*
+ * hgl_laplacian_quadratic -- tr(F^T Delta(w) F) with Delta = I - Theta(w) (Eq. 1), the
+ * first term of the objective P(w) of Eq. 4 (and of the regularised loss), together
+ * with Delta F, whose double is that term's gradient in F.  FP64 throughout: DF by
+ * the operator apply with (a, b) = (1, -1), the trace as the deterministic sum over
+ * all entries of F * DF (fixed-order partial sums).
+ *   w          device FP64[m]
+ *   F          device FP64 panel n x c (ldf)
+ *   DF         device FP64 panel n x c (lddf), out: Delta F (must not alias F)
+ *   value      host out: tr(F^T Delta F)
+ * Synchronises `stream`.
+ */
+hgl_status hgl_laplacian_quadratic(hgl_graph* g, const double* w, const double* F, int64_t ldf,
+                                   double* DF, int64_t lddf, int32_t c, double* value, void* stream);
 
 /* ------------------------------------------------------------------------- */
 /* Adaptive outer iteration (Section 2: F at fixed w, then w at fixed F)      */

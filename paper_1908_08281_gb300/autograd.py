@@ -6,7 +6,8 @@ form of Eq. 4, with the w-gradients computed by the library's kernels.
   M Z = dL/dF with the same operator (M is symmetric), then the bilinear form of the
   Eq. 4 gradient, d/dw_e tr(Z^T Theta F).  Only F is kept from the forward solve; the
   adjoint CG runs its own recurrences.  Y is data: no gradient flows to it.
-* ``laplacian_quadratic(g, w, F)`` -> tr(F^T Delta(w) F), Delta = I - Theta.  Backward:
+* ``laplacian_quadratic(g, w, F)`` -> tr(F^T Delta(w) F), Delta = I - Theta, by
+  ``hgl_laplacian_quadratic`` (the trace is summed in the library).  Backward:
   to w by ``hgl_weight_grad`` (mu = 0, dv(w) included), to F as 2 Delta F by
   ``hgl_apply_theta`` (a = 2, b = -2); both scaled by the incoming scalar gradient.
 
@@ -58,10 +59,10 @@ class _LaplacianQuadratic(torch.autograd.Function):
     @staticmethod
     def forward(ctx, w, F, g):
         Fp = _as_panel(F)
-        DF = hgl.apply_theta(g, w.detach(), Fp, 1.0, -1.0)  # Delta F
+        value, DF = hgl.laplacian_quadratic(g, w.detach(), Fp)  # tr(F^T Delta F), Delta F
         ctx.save_for_backward(w, Fp, DF)
         ctx.g = g
-        return (Fp * DF).sum()
+        return torch.tensor(value, dtype=torch.float64, device=Fp.device)
 
     @staticmethod
     def backward(ctx, go):

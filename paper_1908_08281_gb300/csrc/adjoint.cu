@@ -33,3 +33,31 @@ extern "C" hgl_status hgl_adjoint_grad(hgl_graph* g, const double* w, double lam
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   return solved;
 }
+
+// tr(F^T Delta F) with Delta = I - Theta(w) (the first term of the objective of Eq. 4),
+// and Delta F itself (the loss's F-gradient is 2 Delta F).
+extern "C" hgl_status hgl_laplacian_quadratic(hgl_graph* g, const double* w, const double* F, int64_t ldf,
+                                              double* DF, int64_t lddf, int32_t c, double* value, void* stream) {
+  using namespace hgl;
+  if (!g || !w || !F || !DF || !value) return record_error(HGL_ERR_INVALID_ARG, "NULL argument");
+  if (c < 1) return record_error(HGL_ERR_INVALID_ARG, "c must be >= 1");
+  HGL_TRY(check_panel(F, ldf, c, 8, "F"));
+  HGL_TRY(check_panel(DF, lddf, c, 8, "DF"));
+  if (DF == F) return record_error(HGL_ERR_INVALID_ARG, "DF must not alias F");
+  cudaStream_t st = as_stream(stream);
+  HGL_TRY(degrees_launch(g, w, st));
+  OpCall cl{};
+  cl.g = g;
+  cl.xdt = HGL_FP64;
+  cl.zdt = HGL_FP64;
+  cl.X = F;
+  cl.ldx = ldf;
+  cl.Z = DF;
+  cl.ldz = lddf;
+  cl.c = c;
+  cl.a = 1.0;
+  cl.b = -1.0;
+  cl.epi = EPI_PLAIN;
+  HGL_TRY(op_launch(cl, st, nullptr));
+  return panel_inner(g, F, ldf, DF, lddf, c, st, value);
+}

@@ -91,18 +91,22 @@ __global__ void k_set_target(CgState S, double tol2) {
 
 // Inner-solve targets of a refinement sweep: columns already at tol are frozen
 // (target +inf); the others aim at rr_inner <= rel^2 rr_true, rel = max(inner_tol,
-// 0.1 tol / relres): ten times below what the outer tolerance still needs, so that
-// the FP32 rounding of the correction rarely forces another sweep (a sweep costs a
-// pair-arithmetic residual and a CG restart; the margin costs about one iteration).
+// INNER_MARGIN tol / relres): half of what the outer tolerance still needs.  The
+// other half covers what the recursive FP32 residual does not see -- the rounding of
+// the correction and of F's FP32 pair (a few units of 2^-24 of ||lam Y||), and the
+// error of an FP32 first-residual estimate -- so that another sweep (a pair-arithmetic
+// residual and a CG restart) is rarely needed, without solving past the tolerance.
 // Also sets *S.need = 1 when some column needs the sweep (captured solves zero it
 // before this kernel and guard the sweep's expensive launches with it).
+constexpr double INNER_MARGIN = 0.5;
+
 __global__ void k_inner_targets(CgState S, double tol, double inner_tol) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.c; j += gridDim.x * blockDim.x) {
     const double rel = S.relres[j];
     if (!(S.b2[j] > 0.0) || !(rel > tol) || !isfinite(rel)) {
       S.target[j] = INFINITY;
     } else {
-      double want = fmax(inner_tol, 0.1 * tol / rel);
+      double want = fmax(inner_tol, INNER_MARGIN * tol / rel);
       S.target[j] = want * want * S.rr[j];
       *S.need = 1;
     }
@@ -585,13 +589,18 @@ hgl_status panel_dot_launch(const hgl_graph* g, int c, int dt, const void* A, in
 }
 
 hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out) {
+  return panel_inner(g, F, ldf, F, ldf, c, st, out);
+}
+
+hgl_status panel_inner(const hgl_graph* g, const double* A, int64_t lda, const double* B, int64_t ldb, int c,
+                       cudaStream_t st, double* out) {
   hgl_graph* gg = const_cast<hgl_graph*>(g);
   VecGrid vg = vec_grid(g, c, 8);
   hgl_status stt = HGL_OK;
   double* part = static_cast<double*>(buffer_get(gg->partials, sizeof(double) * 2 * (size_t)std::max(op_partial_rows(g), g->num_sms * 4) * c, &stt));
   if (!part) return stt;
   int rows = 0;
-  HGL_TRY((panel_dot<double, double>(g, c, F, ldf, F, ldf, 1.0, part, st, &rows)));
+  HGL_TRY((panel_dot<double, double>(g, c, A, lda, B, ldb, 1.0, part, st, &rows)));
   std::vector<double> h((size_t)rows * c);
   HGL_CHECK_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));

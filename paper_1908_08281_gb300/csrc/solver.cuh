@@ -101,6 +101,9 @@ hgl_status precond_build(const hgl_graph* g, const double* w, double lam, const 
 
 // sum over all entries of F*F (FP64 panel), deterministic; synchronises the stream.
 hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out);
+// sum over all entries of A*B (FP64 panels), deterministic; synchronises the stream.
+hgl_status panel_inner(const hgl_graph* g, const double* A, int64_t lda, const double* B, int64_t ldb, int c,
+                       cudaStream_t st, double* out);
 
 // Preconditioner hooks (rsvd.cu).  Z = P^-1 R on panels of `dt` (FP64 or FP32) and,
 // when partials_rz is given, per-column partial sums of R.Z (row count in *rows).

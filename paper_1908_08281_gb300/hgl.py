@@ -97,6 +97,7 @@ _SIGNATURES = {
     "hgl_active_set_step": (_I32, [_P, _P, _D, _I64, _P]),
     "hgl_adjoint_grad": (_I32, [_P, _P, _D, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(SolveOpts), _P,
                                 ctypes.POINTER(SolveStats), _P]),
+    "hgl_laplacian_quadratic": (_I32, [_P, _P, _P, _I64, _P, _I64, _I32, ctypes.POINTER(_D), _P]),
     "hgl_adaptive_step": (_I32, [_P, _P, ctypes.POINTER(StepOpts), _P, _I64, _P, _I64, _I32,
                                  ctypes.POINTER(StepStats), _P]),
 }
@@ -474,6 +475,21 @@ def project_simplex(w: torch.Tensor, grad: torch.Tensor | None, eta: float, stre
     _check(lib().hgl_project_simplex(_vec(w, "w"), _vec(grad, "grad") if grad is not None else None, eta,
                                      w.numel(), _stream(stream)))
     return w
+
+
+def laplacian_quadratic(g: Graph, w: torch.Tensor, F: torch.Tensor, DF: torch.Tensor | None = None, stream=None):
+    """tr(F^T Delta F) and Delta F (Eq. 1, Eq. 4); returns (value, DF)."""
+    n, c = F.shape
+    if DF is None:
+        DF = padded_panel(n, c, torch.float64, F.device)
+    pf, ldf, dtf = _panel(F, "F")
+    pd, ldd, dtd = _panel(DF, "DF")
+    if dtf != HGL_FP64 or dtd != HGL_FP64:
+        raise ValueError("F and DF must be float64")
+    val = ctypes.c_double()
+    _check(lib().hgl_laplacian_quadratic(g.handle, _vec(w, "w"), pf, ldf, pd, ldd, c, ctypes.byref(val),
+                                         _stream(stream)))
+    return val.value, DF
 
 
 def adaptive_step(g: Graph, w: torch.Tensor, Y: torch.Tensor, F: torch.Tensor, lam: float, mu: float = 0.0,

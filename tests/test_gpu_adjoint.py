@@ -131,3 +131,22 @@ def test_adjoint_grad_argument_errors():
         hgl.adjoint_grad(g, wt, -1.0, F, _panel(np.ones((d["n"], 2))))
     with pytest.raises(hgl.HglError):
         hgl.adjoint_grad(g, wt, wl.lam, F, F, Z=F)
+
+
+def test_laplacian_quadratic_matches_oracle():
+    """hgl_laplacian_quadratic: tr(F^T Delta F) against the oracle's objective at mu = 0
+    (Eq. 4), and Delta F element-wise against the oracle's operator apply (Eq. 1), on a
+    ragged column count; the trace of a panel of sqrt(dv) columns vanishes (Delta
+    annihilates Dv^1/2 1)."""
+    wl, d, H, w, g, _, _ = _case(3, c=7)
+    wt = torch.tensor(w, device=DEV)
+    F = np.random.default_rng(11).standard_normal((d["n"], d["c"]))
+    val, DF = hgl.laplacian_quadratic(g, wt, _panel(F))
+    ref = core.objective(H, w, F, 0.0)
+    assert abs(val - ref) <= 1e-12 * abs(ref)
+    DFr = core.theta_apply(H, w, F, 1.0, -1.0)
+    assert np.abs(DF.cpu().numpy() - DFr).max() <= 1e-13 * np.abs(DFr).max()
+    dv = np.asarray(H @ w).ravel()
+    S = np.repeat(np.sqrt(dv)[:, None], 2, axis=1)
+    v0, _ = hgl.laplacian_quadratic(g, wt, _panel(S))
+    assert abs(v0) <= 1e-12 * float((S * S).sum())
