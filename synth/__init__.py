@@ -75,7 +75,7 @@ WORKLOADS = {
         rho=0.01, lam=1.0, mu=1e-3, outer=1, tol=1e-10),
     "full_adaptive": Workload(
         "full_adaptive", n=1_000_000, m=2_000_000, sizes=("powerlaw", "mean=10", 2, 2000),
-        c=512, rho=0.005, lam=0.5, mu=0.0, eta=1e-11, outer=20, tol=1e-6,
+        c=512, rho=0.005, lam=0.5, mu=0.0, eta=2e-13, outer=20, tol=1e-6,
         blocks=("sequential", 1024, 8192), k=64, p=10, q=2),
 }
 
