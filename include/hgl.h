@@ -91,7 +91,8 @@ uint64_t hgl_launch_count(void);
                               /* epilogue (FP32 estimate of the mixed solvers, FP64     */
                               /* residual of the FP64 solver)                           */
 #define HGL_PROF_BLOCKSPMM 9  /* block rSVD products Theta_bb S on the sparse route    */
-#define HGL_PROF_FAMILIES 10
+#define HGL_PROF_SCHUR_GEMM 10 /* dense products of the nested Schur-complement inverse */
+#define HGL_PROF_FAMILIES 11
 hgl_status hgl_profile_enable(int32_t on);
 hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches);
 
@@ -351,6 +352,49 @@ hgl_status hgl_block_rsvd(const hgl_graph* g, const double* w, double lam,
 #define HGL_BLOCKS_DENSE  1
 #define HGL_BLOCKS_SPARSE 2
 hgl_status hgl_set_block_product(hgl_graph* g, int32_t mode);
+
+/*
+ * hgl_block_product -- D_b = Theta_bb S_b for every diagonal tessellation block b, the
+ * product that each step of Algorithm 1 (Section 3) applies to the block's basis,
+ * computed as the BF16 block rSVD computes it: the tcgen05 grouped GEMM over the dense
+ * BF16 blocks (S rounded to BF16, FP32 accumulation in TMEM) or the sparse route from
+ * the incidence lists (FP32), as hgl_set_block_product selects.
+ *   w          device FP64[m] weights (sets the graph's degree vectors)
+ *   block_ptr  host int64[nblocks + 1], 0 = b_0 < ... < b_nblocks = n
+ *   l          columns of S and D, 1 .. 96
+ *   S          device FP32, n x l row-major (lds >= l), block b's rows are S_b
+ *   D          device FP32, n x l row-major (ldd >= l), out
+ * Uses the graph's block work space.  Synchronises `stream`; HGL_ERR_TIMEOUT if the
+ * tensor-core GEMM gave up a wait.
+ */
+hgl_status hgl_block_product(const hgl_graph* g, const double* w, const int64_t* block_ptr,
+                             int32_t nblocks, int32_t l, const float* S, int64_t lds, float* D,
+                             int64_t ldd, void* stream);
+
+/*
+ * hgl_schur_inverse -- the nested 2 x 2 Schur-complement inverse of Section 3
+ * (Eqs. 12-14) for the principal submatrix of M = (1+lam) I - Theta(w) on the vertex
+ * range [row0, row0 + nrows), as a dense matrix.  Split in halves 1 | 2:
+ *   M^-1 = [[Z1^-1, -M11^-1 M12 Z2^-1], [-Z2^-1 M21 M11^-1, Z2^-1]],
+ *   Z1 = (1+lam) I - (Theta11 + Theta12 M22^-1 Theta21), Z2 likewise;
+ * M11^-1 and M22^-1 by the same scheme on the halves (nested tessellation) down to
+ * blocks of at most 2 r_min rows; those blocks and the Schur complements Z1, Z2 are
+ * inverted by Algorithm 1 (Rayleigh-Ritz form, FP64): with L the positive
+ * semidefinite part, ((1+lam) I - L)^-1 ~= I/(1+lam) + Q diag(l/((1+lam)(1+lam-l))) Q^T
+ * for the top min(k, size) Ritz pairs from min(k + p, size) columns and q subspace
+ * iterations, the test matrix drawn as for hgl_block_rsvd on the submatrix's global
+ * rows and `seed`.
+ *   dtype      HGL_FP32: the dense products on the tcgen05 tensor cores (TF32 pairs,
+ *              three products per pair, FP32 accumulation: about 2^-21 relative per
+ *              product); HGL_FP64: on FP64 CUDA cores
+ *   Minv       device FP64, nrows x nrows row-major (ldm >= nrows), out
+ * Limits: nrows <= 65,536 (the call allocates about 7 nrows^2 doubles of work space),
+ * k + p <= 96.  Synchronises `stream`; HGL_ERR_TIMEOUT if a tensor-core wait gave up.
+ */
+hgl_status hgl_schur_inverse(const hgl_graph* g, const double* w, double lam, int64_t row0,
+                             int64_t nrows, int32_t r_min, int32_t k, int32_t p, int32_t q,
+                             uint64_t seed, hgl_dtype dtype, double* Minv, int64_t ldm,
+                             void* stream);
 
 /* Release a preconditioner (NULL is a no-op). */
 void hgl_precond_destroy(hgl_precond* P);

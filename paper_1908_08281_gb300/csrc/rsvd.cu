@@ -649,3 +649,119 @@ hgl_status precond_build(const hgl_graph* gc, const double* w, double lam, const
   return s_;
 }
 }  // namespace hgl
+
+// D_b = Theta_bb S_b for every diagonal block, by the products of the BF16 builds (the
+// tcgen05 grouped GEMM over dense BF16 blocks, or the sparse route, as the graph's
+// block-product setting chooses).  Synchronous.
+extern "C" hgl_status hgl_block_product(const hgl_graph* gc, const double* w, const int64_t* block_ptr,
+                                        int32_t nblocks, int32_t l, const float* S, int64_t lds, float* D,
+                                        int64_t ldd, void* stream) {
+  using namespace hgl;
+  hgl_graph* g = const_cast<hgl_graph*>(gc);
+  if (!g || !w || !S || !D) return record_error(HGL_ERR_INVALID_ARG, "NULL argument");
+  if (l < 1 || l > MAX_L) return record_error(HGL_ERR_INVALID_ARG, "l must be in [1, %d]", MAX_L);
+  HGL_TRY(precond_validate(g, block_ptr, nblocks, l, 0, 0, HGL_BF16));
+  if (lds < l || ldd < l) return record_error(HGL_ERR_INVALID_ARG, "leading dimensions must be >= l");
+  cudaStream_t st = as_stream(stream);
+  HGL_TRY(degrees_launch(g, w, st));
+  bool sparse = false;
+  HGL_TRY(block_route_sparse(g, block_ptr, nblocks, st, &sparse));
+  const int lpad = (int)rup(l, 16);
+  Work wk;
+  HGL_TRY(plan(g, g->rsvd, block_ptr, nblocks, l, l, lpad, HGL_BF16, sparse, &wk));
+  const int sms = g->num_sms;
+  hgl_status s_ = HGL_OK;
+  HGL_LPAD_SWITCH(lpad, {
+    if (sparse) {
+      hgl::count_launch();
+      rsvd::k_rows_to_blockrows<LP><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, S, lds, l, static_cast<float*>(wk.Qf));
+    } else {
+      hgl::count_launch(2);
+      rsvd::k_assemble<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
+          wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->s32, g->t32,
+          static_cast<__nv_bfloat16*>(wk.A));
+      rsvd::k_rows_to_st<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, S, lds, l,
+                                                                 static_cast<__nv_bfloat16*>(wk.St));
+    }
+    s_ = cudaGetLastError() == cudaSuccess ? HGL_OK : record_error(HGL_ERR_CUDA, "block product setup launch");
+    if (s_ == HGL_OK) s_ = cudaMemsetAsync(wk.fail, 0, 8, st) == cudaSuccess ? HGL_OK
+                                                                          : record_error(HGL_ERR_CUDA, "memset");
+    if (s_ == HGL_OK) s_ = gemm<LP>(g, wk, HGL_BF16, sms, st);
+    if (s_ == HGL_OK) {
+      hgl::count_launch();
+      rsvd::k_blockrows_to_rows<LP><<<sms * 8, 256, 0, st>>>(wk.B, g->n, static_cast<const float*>(wk.D), l, D, ldd);
+      s_ = cudaGetLastError() == cudaSuccess ? HGL_OK : record_error(HGL_ERR_CUDA, "block product copy-out launch");
+    }
+  });
+  HGL_TRY(s_);
+  int32_t flags[2] = {0, 0};
+  HGL_CHECK_CUDA(cudaMemcpyAsync(flags, wk.fail, 8, cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (flags[1] != 0) return record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
+  return HGL_OK;
+}
+
+namespace hgl {
+
+// Algorithm 1 (Rayleigh-Ritz form, FP64 on CUDA cores) on one dense matrix: the
+// symmetric part of L (nb x nb, row stride ldl), the Gaussian test matrix drawn for the
+// global rows v0 .. v0 + nb - 1 (the same Philox stream as the block preconditioner),
+// l = min(k + p, nb) columns, q subspace iterations.  Writes the kb = min(k, nb) Ritz
+// vectors to Qout (nb x kb, row-major) and the Ritz values, descending, to ev (device,
+// kb entries).  Work space from `space`.  Asynchronous (the plan's metadata upload
+// synchronises).
+hgl_status dense_rsvd_fp64(const double* L, int64_t ldl, int64_t nb, int64_t v0, int k, int p, int q, uint64_t seed,
+                           Buffer& space, double* Qout, double* ev, int* kb_out, cudaStream_t st) {
+  if (nb < 1 || k < 1 || p < 0 || q < 0 || k + p > MAX_L)
+    return record_error(HGL_ERR_INVALID_ARG, "dense rSVD: need nb >= 1, k >= 1, p, q >= 0, k + p <= %d", MAX_L);
+  const int kb = (int)std::min<int64_t>(k, nb);
+  const int l = k + p;
+  const int lpad = (int)rup(l, 16);
+  const int64_t bp[2] = {v0, v0 + nb};
+  // the plan rewrites the work space's metadata with a synchronous copy: let earlier
+  // work on `st` that reads it finish first
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  Work wk;
+  HGL_TRY(plan(nullptr, space, bp, 1, kb, l, lpad, HGL_FP64, false, &wk));
+  int dev = 0, sms = 0;
+  HGL_CHECK_CUDA(cudaGetDevice(&dev));
+  HGL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
+  hgl::count_launch(2);
+  rsvd::k_sym_load<<<sms * 8, 256, 0, st>>>(nb, wk.rows_tot, wk.ldA, L, ldl, static_cast<double*>(wk.A));
+  rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, nullptr, static_cast<double*>(wk.St));
+  HGL_CHECK_CUDA(cudaGetLastError());
+  hgl_status s_ = HGL_OK;
+  HGL_LPAD_SWITCH(lpad, {
+    for (int i = 0; i < 1 + 2 * q && s_ == HGL_OK; ++i) {
+      s_ = gemm<LP>(nullptr, wk, HGL_FP64, sms, st);
+      if (s_ == HGL_OK) s_ = cholqr2<double, double, LP>(wk, HGL_FP64, sms, st, true);
+    }
+    if (s_ == HGL_OK) s_ = gemm<LP>(nullptr, wk, HGL_FP64, sms, st);
+    if (s_ == HGL_OK)
+      s_ = gram<double, LP>(wk, static_cast<const double*>(wk.Qf), static_cast<const double*>(wk.D), st);
+    const size_t jsm = 2 * sizeof(double) * LP * (LP + 1);
+    if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
+    if (s_ == HGL_OK) {
+      hgl::count_launch();
+      rsvd::k_jacobi<double, LP><<<1, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
+    }
+    const size_t rs = sizeof(double) * (LP * LP + 128 * (LP + 1));
+    if (s_ == HGL_OK) s_ = set_smem(rsvd::k_ritz<double, LP>, rs);
+    if (s_ == HGL_OK) {
+      // the Ritz kernel writes row v0 + i of its output: offset the base so that row i
+      // of Qout receives it (only rows v0 .. v0 + nb - 1 are written)
+      hgl::count_launch();
+      const int nu = (int)wk.unit_block.size();
+      rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
+          wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R, Qout - v0 * kb);
+    }
+  });
+  HGL_TRY(s_);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  HGL_CHECK_CUDA(cudaMemcpyAsync(ev, wk.ev, sizeof(double) * kb, cudaMemcpyDeviceToDevice, st));
+  if (kb_out) *kb_out = kb;
+  return HGL_OK;
+}
+
+}  // namespace hgl

@@ -878,3 +878,71 @@ __global__ void __launch_bounds__(256) k_ritz(Blocks B, const int32_t* __restric
 
 }  // namespace rsvd
 }  // namespace hgl
+
+namespace hgl {
+namespace rsvd {
+
+// ---------------------------------------------------------------------------
+// Layout moves for hgl_block_product: a caller's row-major n x l panel S (FP32) into
+// the transposed basis St (lpad x Ktot, zero beyond l and on padding columns) or into
+// the block-row layout of the sparse route (rows_tot x LP, zero-padded), and the
+// block-row product D back into the caller's n x l panel.
+// ---------------------------------------------------------------------------
+template <class TB>
+__global__ void k_rows_to_st(Blocks B, const float* __restrict__ S, int64_t lds, int l, TB* __restrict__ St) {
+  const int64_t total = (int64_t)B.lpad * B.Ktot;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(q / B.Ktot);
+    const int64_t col = q % B.Ktot;
+    const int b = find_block(B.koff, B.nb, col);
+    const int64_t i = col - B.koff[b];
+    const float x = (j < l && i < B.rows[b]) ? S[(B.v0[b] + i) * lds + j] : 0.f;
+    St[(int64_t)j * B.Ktot + col] = from_double<TB>((double)x);
+  }
+}
+
+template <int LP>
+__global__ void k_rows_to_blockrows(Blocks B, int64_t rows_tot, const float* __restrict__ S, int64_t lds, int l,
+                                    float* __restrict__ Qf) {
+  const int64_t total = rows_tot * LP;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = q / LP;
+    const int j = (int)(q % LP);
+    const int b = find_block(B.arow, B.nb, r);
+    const int64_t i = r - B.arow[b];
+    Qf[q] = (j < l && i < B.rows[b]) ? S[(B.v0[b] + i) * lds + j] : 0.f;
+  }
+}
+
+template <int LP>
+__global__ void k_blockrows_to_rows(Blocks B, int64_t n, const float* __restrict__ Dw, int l, float* __restrict__ D,
+                                    int64_t ldd) {
+  const int64_t total = n * l;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = q / l;
+    const int j = (int)(q % l);
+    const int b = find_block(B.v0, B.nb, v);
+    D[v * ldd + j] = Dw[(B.arow[b] + (v - B.v0[b])) * LP + j];
+  }
+}
+
+}  // namespace rsvd
+}  // namespace hgl
+
+namespace hgl {
+namespace rsvd {
+
+// The symmetric part of a dense nb x nb matrix L into the block storage of a single
+// block: A[i, j] = (L[i, j] + L[j, i]) / 2 for i, j < nb; zero elsewhere in the rows_tot
+// x ldA storage (padding rows and columns).
+static __global__ void k_sym_load(int64_t nb, int64_t rows_tot, int64_t ldA, const double* __restrict__ L, int64_t ldl,
+                           double* __restrict__ A) {
+  const int64_t total = rows_tot * ldA;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / ldA, j = q % ldA;
+    A[q] = (i < nb && j < nb) ? 0.5 * (L[i * ldl + j] + L[j * ldl + i]) : 0.0;
+  }
+}
+
+}  // namespace rsvd
+}  // namespace hgl

@@ -90,6 +90,8 @@ _SIGNATURES = {
     "hgl_precond_apply": (_I32, [_P, _P, _I64, _P, _I64, _I32, _I32, _P]),
     "hgl_precond_tensor_cores": (_I32, [_P, _I32, ctypes.POINTER(_I32)]),
     "hgl_set_block_product": (_I32, [_P, _I32]),
+    "hgl_block_product": (_I32, [_P, _P, ctypes.POINTER(_I64), _I32, _I32, _P, _I64, _P, _I64, _P]),
+    "hgl_schur_inverse": (_I32, [_P, _P, _D, _I64, _I64, _I32, _I32, _I32, _I32, _U64, _I32, _P, _I64, _P]),
     "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
     "hgl_block_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
@@ -127,11 +129,12 @@ def launch_count() -> int:
 
 PROF_OPERATOR, PROF_RESIDUAL, PROF_GEMM, PROF_GRADIENT = 0, 1, 2, 3
 PROF_PRECOND, PROF_RSVD, PROF_VECTOR, PROF_PROJECT, PROF_OPRESID, PROF_BLOCKSPMM = 4, 5, 6, 7, 8, 9
+PROF_SCHUR_GEMM = 10
 HGL_BLOCKS_AUTO, HGL_BLOCKS_DENSE, HGL_BLOCKS_SPARSE = 0, 1, 2
 PROF_NAMES = {0: "operator apply", 1: "pair-arithmetic residual", 2: "grouped block GEMM (tcgen05)",
               3: "weight gradient", 4: "preconditioner apply", 5: "block rSVD build (all)",
               6: "CG vector kernels", 7: "simplex projection", 8: "residual by one operator pass",
-              9: "sparse block products (rSVD)"}
+              9: "sparse block products (rSVD)", 10: "Schur-inverse dense products"}
 
 
 def profile_enable(on: bool = True):
@@ -399,6 +402,28 @@ def precond_apply(P: Precond, R: torch.Tensor, Z: torch.Tensor | None = None, st
     pz, ldz, _ = _panel(Z, "Z")
     _check(lib().hgl_precond_apply(P.handle, pr, ldr, pz, ldz, c, dt, _stream(stream)))
     return Z
+
+
+def block_product(g: Graph, w: torch.Tensor, block_ptr, S: torch.Tensor, stream=None) -> torch.Tensor:
+    """D_b = Theta_bb S_b per diagonal block (Algorithm 1's products, BF16 route)."""
+    if S.dtype != torch.float32 or S.stride(1) != 1:
+        raise ValueError("S must be a row-major float32 panel")
+    n, l = S.shape
+    D = torch.empty((n, l), dtype=torch.float32, device=S.device)
+    bp = (ctypes.c_int64 * len(block_ptr))(*[int(x) for x in block_ptr])
+    _check(lib().hgl_block_product(g.handle, _vec(w, "w"), bp, len(block_ptr) - 1, l,
+                                   ctypes.c_void_p(S.data_ptr()), S.stride(0), ctypes.c_void_p(D.data_ptr()),
+                                   D.stride(0), _stream(stream)))
+    return D
+
+
+def schur_inverse(g: Graph, w: torch.Tensor, lam: float, row0: int, nrows: int, r_min: int, k: int, p: int,
+                  q: int, seed: int, dtype: int = HGL_FP32, stream=None) -> torch.Tensor:
+    """Dense approximate inverse of M on [row0, row0 + nrows) by the nested Schur scheme."""
+    out = torch.empty((nrows, nrows), dtype=torch.float64, device=w.device)
+    _check(lib().hgl_schur_inverse(g.handle, _vec(w, "w"), lam, row0, nrows, r_min, k, p, q, seed, dtype,
+                                   ctypes.c_void_p(out.data_ptr()), nrows, _stream(stream)))
+    return out
 
 
 def selftest_wait_timeout(limit_cycles: int, stream=None):
