@@ -521,16 +521,18 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
   };
 
   if (extras && extras->fixed_iters > 0) {
-    // capture mode: a fixed launch sequence without host reads -- the residual, then two
-    // guarded sweeps (the first two of the eager loop) each followed by a guarded
-    // residual; the second runs, on the device's decision, only when the first fell
-    // short of tol (one FP32 sweep reaches about 1e-7 times the starting relres and at
-    // most the inner floor).  Statistics stay on the device.
-    if (mode == HGL_BF16) return record_error(HGL_ERR_INVALID_ARG, "captured solves take FP64 or FP32 panels");
+    // capture mode: a fixed launch sequence without host reads -- the residual, then
+    // guarded sweeps (the first ones of the eager loop) each followed by a guarded
+    // residual; a sweep runs, on the device's decision, only when the previous one fell
+    // short of tol.  One FP32 sweep reaches about 1e-7 times the starting relres and at
+    // most the inner floor, so two suffice; a BF16 sweep gains about 1e-2 (the BF16
+    // rounding of the search directions bounds the inner solve), so BF16 panels get
+    // four.  Statistics stay on the device.
     const double floor = inner_tol;
+    const int nsweeps = mode == HGL_BF16 ? 4 : 2;
     int done = 0;
     HGL_TRY(cheap_first ? residual_f32() : residual(nullptr));
-    for (int sw = 0; sw < 2; ++sw) {
+    for (int sw = 0; sw < nsweeps; ++sw) {
       HGL_TRY(sweep(floor, extras->fixed_iters, 0, &done, true));
       // after an FP32 estimate the pair residual runs even when the sweep was skipped:
       // the estimate is never the reported relres

@@ -350,8 +350,8 @@ hgl_status step_replay(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o, hgl_
 hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, const double* Y, int64_t ldy,
                               double* F, int64_t ldf, int c, hgl_step_stats* stats, cudaStream_t st) {
   if (!(o.flags & HGL_STEP_GRAPH)) return adaptive_step_eager(g, w, o, Y, ldy, F, ldf, c, stats, st);
-  if (o.solve.dtype != HGL_FP64 && o.solve.dtype != HGL_FP32)
-    return record_error(HGL_ERR_INVALID_ARG, "a captured step takes FP64 or FP32 solves");
+  if (o.solve.dtype != HGL_FP64 && o.solve.dtype != HGL_FP32 && o.solve.dtype != HGL_BF16)
+    return record_error(HGL_ERR_INVALID_ARG, "unknown solve dtype");
   StepGraph*& sg = g->step_graph;
   if (!sg || !sg->matches(w, o, Y, ldy, F, ldf, c)) {
     // a new call pattern: run it eagerly (which also sizes every work buffer the graph
@@ -374,7 +374,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
     ng->route = o.route;
     ng->flags = o.flags;
     ng->solve = o.solve;
-    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-5;
+    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : (o.solve.dtype == HGL_BF16 ? 1e-2 : 1e-5);
     ng->fixed_iters = cg_iteration_bound(o.lam, o.solve.dtype == HGL_FP64 ? (o.solve.tol > 0 ? o.solve.tol : 1e-10)
                                                                            : floor) + 4;
     hgl_status e = HGL_OK;
@@ -385,7 +385,8 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
       ng->q = o.q;
       e = precond_plan_create(g, o.lam, o.block_ptr, o.nblocks, o.k, o.p, o.q, HGL_BF16, true, st, &ng->plan);
       if (e == HGL_OK)
-        e = precond_reserve(const_cast<hgl_precond*>(precond_plan_handle(ng->plan)), c, o.solve.dtype);
+        e = precond_reserve(const_cast<hgl_precond*>(precond_plan_handle(ng->plan)), c,
+                            o.solve.dtype == HGL_FP64 ? HGL_FP64 : HGL_FP32);
     }
     if (e == HGL_OK) {
       const cudaError_t ce = cudaMalloc(&ng->seed_dev, sizeof(uint64_t));

@@ -287,6 +287,8 @@ def test_precond_apply_fp32_matches_definition(k, c, tc):
 
 @pytest.mark.parametrize("route,dtype,tol", [(hgl.HGL_ROUTE_BR, hgl.HGL_FP32, 1e-8),
                                              (hgl.HGL_ROUTE_BR, hgl.HGL_FP32, 3e-6),
+                                             (hgl.HGL_ROUTE_BR, hgl.HGL_BF16, 3e-6),
+                                             (hgl.HGL_ROUTE_CG, hgl.HGL_BF16, 1e-6),
                                              (hgl.HGL_ROUTE_CG, hgl.HGL_FP64, 1e-10)])
 def test_captured_step_matches_oracle_each_step(route, dtype, tol):
     """HGL_STEP_GRAPH: the first call runs eagerly, the second captures the step into a
@@ -348,11 +350,3 @@ def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs():
         assert rel.max() <= tol and st.solve.relres_max <= tol, (i, rel.max(), st.solve.relres_max)
         assert np.isclose(st.solve.relres_max, rel.max(), rtol=1e-3, atol=1e-13), (i, rel.max(), st.solve.relres_max)
     assert np.allclose(wt.cpu().numpy(), w, rtol=1e-12, atol=0)
-
-
-def test_captured_step_rejects_bf16_panels():
-    wl, d, H, w, g = _setup(n=600, m=900, c=2, seed=13)
-    wt = torch.tensor(d["w0"], device=DEV)
-    with pytest.raises(hgl.HglError):
-        hgl.adaptive_step(g, wt, _panel(d["Y"]), hgl.padded_panel(d["n"], d["c"]), wl.lam, 0.0, 1e-3,
-                          dtype=hgl.HGL_BF16, flags=hgl.HGL_STEP_GRAPH)
