@@ -110,8 +110,9 @@ struct Work {
 
 inline size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
 
-hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, int l, int lpad, int dtype,
-                bool sparse, Work* w) {
+// Blocks given by their first global row v0s[b] and size sizes[b] (any ranges).
+hgl_status plan_blocks(Buffer& space, const int64_t* v0s, const int64_t* sizes, int nb, int k, int l, int lpad,
+                       int dtype, bool sparse, Work* w) {
   const bool bf16 = dtype == HGL_BF16;
   w->sparse = sparse;
   w->v0.resize(nb);
@@ -122,8 +123,8 @@ hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, i
   w->kb.resize(nb);
   int64_t maxb = 0;
   for (int b = 0; b < nb; ++b) {
-    const int64_t sz = bp[b + 1] - bp[b];
-    w->v0[b] = bp[b];
+    const int64_t sz = sizes[b];
+    w->v0[b] = v0s[b];
     w->rows[b] = (int32_t)sz;
     w->arow[b] = w->rows_tot;
     w->koff[b] = w->Ktot;
@@ -211,6 +212,15 @@ hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, i
   return HGL_OK;
 }
 
+// Contiguous tessellation blocks [bp[b], bp[b + 1]).
+hgl_status plan(hgl_graph* g, Buffer& space, const int64_t* bp, int nb, int k, int l, int lpad, int dtype,
+                bool sparse, Work* w) {
+  (void)g;
+  std::vector<int64_t> v0s(bp, bp + nb), sizes(nb);
+  for (int b = 0; b < nb; ++b) sizes[b] = bp[b + 1] - bp[b];
+  return plan_blocks(space, v0s.data(), sizes.data(), nb, k, l, lpad, dtype, sparse, w);
+}
+
 template <class F>
 hgl_status set_smem(F* fn, size_t bytes) {
   HGL_CHECK_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(fn), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -265,9 +275,12 @@ hgl_status gram(const Work& w, const T* X, const T* Y, cudaStream_t st) {
 }
 
 // Q = CholeskyQR2(D): G = D^T D, Rinv = chol^-T, Qf = D Rinv; again on Qf.  The final
-// pass also refreshes the transposed basis St (when write_st).
+// pass also refreshes the transposed basis St (when write_st).  passes = 1 stops after
+// the first (shifted) factorisation: a basis of the same span whose orthonormality is
+// off by about the shift over the smallest squared singular value -- enough between
+// the products of the subspace iteration, whose last orthonormalisation takes both.
 template <class T, class TB, int LP>
-hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool write_st) {
+hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool write_st, int passes = 2) {
   const int nb = w.B.nb;
   const int nu = (int)w.unit_block.size();
   const size_t chol_smem = 2 * sizeof(double) * LP * (LP + 1);
@@ -280,10 +293,10 @@ hgl_status cholqr2(const Work& w, int dtype, int sms, cudaStream_t st, bool writ
   const double drop = dtype == HGL_BF16 ? 1e-6 : 1e-13;
   const T* Y = static_cast<const T*>(w.D);
   T* Qf = static_cast<T*>(w.Qf);
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < passes; ++pass) {
     HGL_TRY((gram<T, LP>(w, Y, Y, st)));
     hgl::count_launch(); rsvd::k_chol_inv<LP><<<nb, 256, chol_smem, st>>>(w.B, w.G, pass == 0 ? shift : 0.0, drop, w.R, w.fail);
-    const bool last = pass == 1;
+    const bool last = pass == passes - 1;
     // in-place on the second pass is fine: each tile reads its rows before writing them
     hgl::count_launch(); rsvd::k_apply_rinv<T, TB, LP><<<std::min(nu, sms * 4), 256, ap_smem, st>>>(
         w.B, w.d_unit_block, w.d_unit_tile, nu, Y, w.R, Qf, (last && write_st) ? static_cast<TB*>(w.St) : nullptr);
@@ -560,8 +573,10 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
   HGL_LPAD_SWITCH(lpad, {
     for (int i = 0; i < nprod && s_ == HGL_OK; ++i) {
       s_ = gemm<LP>(g, wk, gemm_dtype, sms, st);
+      // BF16 route: one CholeskyQR pass between products, two for the final basis (the
+      // FP64 checking route keeps two throughout)
       if (s_ == HGL_OK)
-        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, !wk.sparse)
+        s_ = bf16 ? cholqr2<float, __nv_bfloat16, LP>(wk, gemm_dtype, sms, st, !wk.sparse, i + 1 < nprod ? 1 : 2)
                   : cholqr2<double, double, LP>(wk, gemm_dtype, sms, st, true);
     }
     if (s_ == HGL_OK) s_ = gemm<LP>(g, wk, gemm_dtype, sms, st);
@@ -703,32 +718,37 @@ extern "C" hgl_status hgl_block_product(const hgl_graph* gc, const double* w, co
 
 namespace hgl {
 
-// Algorithm 1 (Rayleigh-Ritz form, FP64 on CUDA cores) on one dense matrix: the
-// symmetric part of L (nb x nb, row stride ldl), the Gaussian test matrix drawn for the
-// global rows v0 .. v0 + nb - 1 (the same Philox stream as the block preconditioner),
-// l = min(k + p, nb) columns, q subspace iterations.  Writes the kb = min(k, nb) Ritz
-// vectors to Qout (nb x kb, row-major) and the Ritz values, descending, to ev (device,
-// kb entries).  Work space from `space`.  Asynchronous (the plan's metadata upload
-// synchronises).
-hgl_status dense_rsvd_fp64(const double* L, int64_t ldl, int64_t nb, int64_t v0, int k, int p, int q, uint64_t seed,
-                           Buffer& space, double* Qout, double* ev, int* kb_out, cudaStream_t st) {
+// Algorithm 1 (Rayleigh-Ritz form, FP64 on CUDA cores) on nb dense matrices at once:
+// the symmetric part of L_b (sizes[b] x sizes[b], row stride ldls[b], device pointer
+// Ls[b]), the Gaussian test matrix drawn for the global rows v0s[b] .. (the same Philox
+// stream as the block preconditioner), l = min(k + p, size) columns, q subspace
+// iterations; every step one launch for all matrices.  Ritz vectors of matrix b go to
+// rows v0s[b] - qrow0 .. of Qout (row-major, k columns; columns past min(k, size) are
+// zero), its Ritz values, descending, to ev[b * k ..].  The row ranges must not overlap.
+// Work space from `space`.  Asynchronous after the plan's metadata upload (which first
+// lets earlier work on `st` finish: it rewrites metadata that work may read).
+hgl_status dense_rsvd_batch_fp64(int nb, const double* const* Ls, const int64_t* ldls, const int64_t* v0s,
+                                 const int64_t* sizes, int k, int p, int q, uint64_t seed, Buffer& space,
+                                 double* Qout, int64_t qrow0, double* ev, cudaStream_t st) {
   if (nb < 1 || k < 1 || p < 0 || q < 0 || k + p > MAX_L)
     return record_error(HGL_ERR_INVALID_ARG, "dense rSVD: need nb >= 1, k >= 1, p, q >= 0, k + p <= %d", MAX_L);
-  const int kb = (int)std::min<int64_t>(k, nb);
   const int l = k + p;
   const int lpad = (int)rup(l, 16);
-  const int64_t bp[2] = {v0, v0 + nb};
-  // the plan rewrites the work space's metadata with a synchronous copy: let earlier
-  // work on `st` that reads it finish first
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   Work wk;
-  HGL_TRY(plan(nullptr, space, bp, 1, kb, l, lpad, HGL_FP64, false, &wk));
+  HGL_TRY(plan_blocks(space, v0s, sizes, nb, k, l, lpad, HGL_FP64, false, &wk));
   int dev = 0, sms = 0;
   HGL_CHECK_CUDA(cudaGetDevice(&dev));
   HGL_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
-  hgl::count_launch(2);
-  rsvd::k_sym_load<<<sms * 8, 256, 0, st>>>(nb, wk.rows_tot, wk.ldA, L, ldl, static_cast<double*>(wk.A));
+  double* A = static_cast<double*>(wk.A);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t rows_b = rup(sizes[b], 128);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows_b * wk.ldA + 255) / 256, sms * 8));
+    hgl::count_launch();
+    rsvd::k_sym_load<<<grid, 256, 0, st>>>(sizes[b], rows_b, wk.ldA, Ls[b], ldls[b], A + wk.arow[b] * wk.ldA);
+  }
+  hgl::count_launch();
   rsvd::k_omega<double><<<sms * 8, 256, 0, st>>>(wk.B, seed, nullptr, static_cast<double*>(wk.St));
   HGL_CHECK_CUDA(cudaGetLastError());
   hgl_status s_ = HGL_OK;
@@ -744,23 +764,26 @@ hgl_status dense_rsvd_fp64(const double* L, int64_t ldl, int64_t nb, int64_t v0,
     if (s_ == HGL_OK) s_ = set_smem(rsvd::k_jacobi<double, LP>, jsm);
     if (s_ == HGL_OK) {
       hgl::count_launch();
-      rsvd::k_jacobi<double, LP><<<1, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
+      rsvd::k_jacobi<double, LP><<<nb, 256, jsm, st>>>(wk.B, wk.G, wk.R, wk.ev, 40, 1e-30);
     }
     const size_t rs = sizeof(double) * (LP * LP + 128 * (LP + 1));
     if (s_ == HGL_OK) s_ = set_smem(rsvd::k_ritz<double, LP>, rs);
     if (s_ == HGL_OK) {
-      // the Ritz kernel writes row v0 + i of its output: offset the base so that row i
-      // of Qout receives it (only rows v0 .. v0 + nb - 1 are written)
+      // the Ritz kernel writes global row v0 + i of its output: offset the base so that
+      // row v0 + i - qrow0 of Qout receives it
       hgl::count_launch();
       const int nu = (int)wk.unit_block.size();
       rsvd::k_ritz<double, LP><<<std::min(nu, sms * 4), 256, rs, st>>>(
-          wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R, Qout - v0 * kb);
+          wk.B, wk.d_unit_block, wk.d_unit_tile, nu, static_cast<const double*>(wk.Qf), wk.R, Qout - qrow0 * k);
+    }
+    if (s_ == HGL_OK) {
+      const cudaError_t ce = cudaMemcpy2DAsync(ev, sizeof(double) * k, wk.ev, sizeof(double) * LP, sizeof(double) * k,
+                                               nb, cudaMemcpyDeviceToDevice, st);
+      if (ce != cudaSuccess) s_ = cuda_error(ce, "Ritz values", __FILE__, __LINE__);
     }
   });
   HGL_TRY(s_);
   HGL_CHECK_CUDA(cudaGetLastError());
-  HGL_CHECK_CUDA(cudaMemcpyAsync(ev, wk.ev, sizeof(double) * kb, cudaMemcpyDeviceToDevice, st));
-  if (kb_out) *kb_out = kb;
   return HGL_OK;
 }
 

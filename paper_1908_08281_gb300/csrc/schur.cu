@@ -312,11 +312,10 @@ k_gemm_tf32x3(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
 namespace hgl {
 namespace {
 
-inline int64_t rup64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// Device memory for one call: a bump arena (one allocation) for the recursion's dense
-// temporaries, the split operands of the tensor-core products, the work space of
-// Algorithm 1 and the error word of the tcgen05 kernel.
+inline int64_t rup64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline size_t dbytes(int64_t count) { return (size_t)rup64(count * (int64_t)sizeof(double), 256); }
+
 struct SchurCtx {
   int dtype = HGL_FP64;
   double lam = 0.0;
@@ -324,34 +323,10 @@ struct SchurCtx {
   uint64_t seed = 0;
   int sms = 0;
   cudaStream_t st = nullptr;
-  char* arena = nullptr;
-  size_t arena_bytes = 0, arena_top = 0;
-  Buffer split;   // Ah, Al, Bh, Bl (FP32)
+  Buffer split;   // Ah, Al, Bh, Bl (FP32) of the tensor-core products
   Buffer rsvd;    // Algorithm 1's work space
   int* err = nullptr;
-  int64_t launches_tc = 0;
-
-  double* take(int64_t count) {
-    const size_t bytes = (size_t)rup64(count * (int64_t)sizeof(double), 256);
-    if (arena_top + bytes > arena_bytes) return nullptr;
-    double* p_ = reinterpret_cast<double*>(arena + arena_top);
-    arena_top += bytes;
-    return p_;
-  }
 };
-
-inline size_t dbytes(int64_t count) { return (size_t)rup64(count * (int64_t)sizeof(double), 256); }
-
-// Arena bytes a node of size n needs (itself and, one after another, its children).
-size_t schur_need(int64_t n, int r_min, int k) {
-  const int64_t kb = std::min<int64_t>(k, n);
-  if (n <= 2 * (int64_t)r_min) return dbytes(n * kb) * 2 + dbytes(kb);
-  const int64_t h = n / 2, h2 = n - h, mx = std::max(h, h2);
-  const size_t own = dbytes(h * h) + dbytes(h2 * h2);
-  const size_t products = dbytes(h * h2) + dbytes(mx * mx) + 2 * dbytes(mx * std::min<int64_t>(k, mx)) +
-                          dbytes(std::min<int64_t>(k, mx));
-  return own + std::max({schur_need(h, r_min, k), schur_need(h2, r_min, k), products});
-}
 
 // C (M x N) = A (M x K) op(B) (+ C0): tcgen05 3xTF32 for HGL_FP32 when every side is at
 // least 128, else FP64 CUDA cores.
@@ -398,7 +373,6 @@ hgl_status dense_gemm(SchurCtx& cx, int64_t M, int64_t N, int64_t K, const doubl
       k_gemm_tf32x3<<<std::min(a.nunits, cx.sms), 256, TG_SMEM, cx.st>>>(mAh, mAl, mBh, mBl, a);
     }
     HGL_CHECK_CUDA(cudaGetLastError());
-    ++cx.launches_tc;
     return HGL_OK;
   }
   dim3 grid((unsigned)((N + DG_T - 1) / DG_T), (unsigned)((M + DG_T - 1) / DG_T));
@@ -411,69 +385,71 @@ hgl_status dense_gemm(SchurCtx& cx, int64_t M, int64_t N, int64_t K, const doubl
   return HGL_OK;
 }
 
-// out (nb x nb, ldo) = ((1+lam) I - L)^-1 from Algorithm 1 on L's symmetric part:
-// I/(1+lam) + (Q diag(g)) Q^T.  Temporaries from the arena (released on return).
-hgl_status lowrank_inverse(SchurCtx& cx, const double* L, int64_t ldl, int64_t nb, int64_t v0, double* out,
-                           int64_t ldo) {
-  const size_t top = cx.arena_top;
-  const int64_t kb = std::min<int64_t>(cx.k, nb);
-  double* Q = cx.take(nb * kb);
-  double* Qg = cx.take(nb * kb);
-  double* ev = cx.take(kb);
-  if (!Q || !Qg || !ev) return record_error(HGL_ERR_OOM, "Schur inverse: arena exhausted");
-  int kbo = 0;
-  HGL_TRY(dense_rsvd_fp64(L, ldl, nb, v0, cx.k, cx.p, cx.q, cx.seed, cx.rsvd, Q, ev, &kbo, cx.st));
-  count_launch();
-  k_gain_cols<<<cx.sms * 4, 256, 0, cx.st>>>(nb, kbo, Q, ev, cx.lam, Qg);
-  HGL_CHECK_CUDA(cudaGetLastError());
-  // the rank-kb outer product on CUDA cores in FP64 (nb x nb x kb, small)
-  dim3 grid((unsigned)((nb + DG_T - 1) / DG_T), (unsigned)((nb + DG_T - 1) / DG_T));
-  count_launch(2);
-  k_dgemm<<<grid, 256, 0, cx.st>>>(nb, nb, kbo, Qg, kbo, Q, kbo, 1, nullptr, 0, out, ldo);
-  k_add_diag<<<std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, cx.sms * 4)), 256, 0, cx.st>>>(
-      nb, 1.0 / (1.0 + cx.lam), out, ldo);
-  HGL_CHECK_CUDA(cudaGetLastError());
-  cx.arena_top = top;
-  return HGL_OK;
+// One node of the nested tessellation: rows [off, off + n) of the range (offsets into the
+// dense Theta), its inverse in `out` (ld ldo), its halves' nodes (internal nodes).
+struct Node {
+  int64_t off = 0, n = 0;
+  int level = 0;
+  int child[2] = {-1, -1};
+  double* out = nullptr;
+  int64_t ldo = 0;
+};
+
+int build_tree(std::vector<Node>& nodes, int64_t off, int64_t n, int level, int r_min) {
+  const int id = (int)nodes.size();
+  nodes.push_back(Node{});
+  nodes[id].off = off;
+  nodes[id].n = n;
+  nodes[id].level = level;
+  if (n > 2 * (int64_t)r_min) {
+    const int64_t h = n / 2;
+    const int c0 = build_tree(nodes, off, h, level + 1, r_min);
+    const int c1 = build_tree(nodes, off + h, n - h, level + 1, r_min);
+    nodes[id].child[0] = c0;
+    nodes[id].child[1] = c1;
+  }
+  return id;
 }
 
-// out (n x n, ldo) ~= ((1+lam) I - T)^-1 for the dense symmetric T (n x n, ldt) whose
-// rows are the global rows v0 .. v0 + n - 1 (Eqs. 12-14, nested).
-hgl_status schur_rec(SchurCtx& cx, const double* T, int64_t ldt, int64_t n, int64_t v0, double* out, int64_t ldo) {
-  if (n <= 2 * (int64_t)cx.r_min) return lowrank_inverse(cx, T, ldt, n, v0, out, ldo);
-  const size_t top = cx.arena_top;
-  const int64_t h = n / 2, h2 = n - h, mx = std::max(h, h2);
-  const double* T11 = T;
-  const double* T12 = T + h;
-  const double* T21 = T + h * ldt;
-  const double* T22 = T + h * ldt + h;
-  double* inv11 = cx.take(h * h);
-  double* inv22 = cx.take(h2 * h2);
-  if (!inv11 || !inv22) return record_error(HGL_ERR_OOM, "Schur inverse: arena exhausted");
-  HGL_TRY(schur_rec(cx, T11, ldt, h, v0, inv11, h));
-  HGL_TRY(schur_rec(cx, T22, ldt, h2, v0 + h, inv22, h2));
-  double* X = cx.take(h * h2);   // h x h2 or h2 x h
-  double* Lb = cx.take(mx * mx);
-  if (!X || !Lb) return record_error(HGL_ERR_OOM, "Schur inverse: arena exhausted");
-  double* O11 = out;
-  double* O12 = out + h;
-  double* O21 = out + h * ldo;
-  double* O22 = out + h * ldo + h;
-  // Z1^-1: L1 = T11 + (T12 M22^-1) T21
-  HGL_TRY(dense_gemm(cx, h, h2, h2, T12, ldt, inv22, h2, false, nullptr, 0, X, h2));
-  HGL_TRY(dense_gemm(cx, h, h, h2, X, h2, T21, ldt, false, T11, ldt, Lb, h));
-  HGL_TRY(lowrank_inverse(cx, Lb, h, h, v0, O11, ldo));
-  // Z2^-1: L2 = T22 + (T21 M11^-1) T12
-  HGL_TRY(dense_gemm(cx, h2, h, h, T21, ldt, inv11, h, false, nullptr, 0, X, h));
-  HGL_TRY(dense_gemm(cx, h2, h2, h, X, h, T12, ldt, false, T22, ldt, Lb, h2));
-  HGL_TRY(lowrank_inverse(cx, Lb, h2, h2, v0 + h, O22, ldo));
-  // off-diagonal blocks: -M11^-1 M12 Z2^-1 = (M11^-1 T12) Z2^-1 and
-  // -Z2^-1 M21 M11^-1 = (Z2^-1 T21) M11^-1
-  HGL_TRY(dense_gemm(cx, h, h2, h, inv11, h, T12, ldt, false, nullptr, 0, X, h2));
-  HGL_TRY(dense_gemm(cx, h, h2, h2, X, h2, O22, ldo, false, nullptr, 0, O12, ldo));
-  HGL_TRY(dense_gemm(cx, h2, h, h2, O22, ldo, T21, ldt, false, nullptr, 0, X, h));
-  HGL_TRY(dense_gemm(cx, h2, h, h, X, h, inv11, h, false, nullptr, 0, O21, ldo));
-  cx.arena_top = top;
+// One item of a level's batched Algorithm 1: the matrix L (a leaf's diagonal block of
+// Theta, or a Schur complement's L), its global first row, and where its low-rank
+// inverse ((1+lam) I - L)^-1 goes.
+struct Item {
+  const double* L;
+  int64_t ldl, v0, n;
+  double* out;
+  int64_t ldo;
+};
+
+// The level's inverses: Algorithm 1 on all items in one batch, then per item
+// out = I/(1+lam) + (Q diag(g)) Q^T with g = l/((1+lam)(1+lam-l)), l = max(Ritz value, 0).
+hgl_status lowrank_inverses(SchurCtx& cx, const std::vector<Item>& items, int64_t row0, double* Q, double* Qg,
+                            double* ev) {
+  const int nb = (int)items.size();
+  std::vector<const double*> Ls(nb);
+  std::vector<int64_t> ld(nb), v0(nb), sz(nb);
+  for (int b = 0; b < nb; ++b) {
+    Ls[b] = items[b].L;
+    ld[b] = items[b].ldl;
+    v0[b] = items[b].v0;
+    sz[b] = items[b].n;
+  }
+  HGL_TRY(dense_rsvd_batch_fp64(nb, Ls.data(), ld.data(), v0.data(), sz.data(), cx.k, cx.p, cx.q, cx.seed, cx.rsvd,
+                                Q, row0, ev, cx.st));
+  for (int b = 0; b < nb; ++b) {
+    const Item& it = items[b];
+    // Q's columns past min(k, n) are zero, so all k columns can take part
+    double* Qb = Q + (it.v0 - row0) * cx.k;
+    double* Qgb = Qg + (it.v0 - row0) * cx.k;
+    count_launch(3);
+    k_gain_cols<<<cx.sms * 4, 256, 0, cx.st>>>(it.n, cx.k, Qb, ev + (size_t)b * cx.k, cx.lam, Qgb);
+    // the low-rank outer product on CUDA cores in FP64 (n x n x k)
+    dim3 grid((unsigned)((it.n + DG_T - 1) / DG_T), (unsigned)((it.n + DG_T - 1) / DG_T));
+    k_dgemm<<<grid, 256, 0, cx.st>>>(it.n, it.n, cx.k, Qgb, cx.k, Qb, cx.k, 1, nullptr, 0, it.out, it.ldo);
+    k_add_diag<<<(int)std::max<int64_t>(1, std::min<int64_t>((it.n + 255) / 256, cx.sms * 4)), 256, 0, cx.st>>>(
+        it.n, 1.0 / (1.0 + cx.lam), it.out, it.ldo);
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
   return HGL_OK;
 }
 
@@ -505,63 +481,143 @@ extern "C" hgl_status hgl_schur_inverse(const hgl_graph* gc, const double* w, do
   cx.seed = seed;
   cx.sms = g->num_sms;
   cx.st = st;
-  // the dense Theta of the range (FP64, assembled from the incidence lists) and the arena
+
+  // the nested tessellation, its levels, and one arena: the dense Theta of the range,
+  // every non-root node's inverse, one level's Schur-complement matrices, a product
+  // temporary, and the Ritz vectors
+  std::vector<Node> nodes;
+  build_tree(nodes, 0, nrows, 0, r_min);
+  int depth = 0;
+  for (const Node& nd : nodes) depth = std::max(depth, nd.level);
   const int64_t ldt = rup64(nrows, 64), trows = rup64(nrows, 128);
-  const size_t tbytes = dbytes(trows * ldt);
-  cx.arena_bytes = tbytes + schur_need(nrows, r_min, k) + 256;
-  void* mem = nullptr;
-  HGL_CHECK_CUDA(cudaMalloc(&mem, cx.arena_bytes));
-  cx.arena = static_cast<char*>(mem);
+  size_t bytes = dbytes(trows * ldt);
+  for (size_t i = 1; i < nodes.size(); ++i) bytes += dbytes(nodes[i].n * nodes[i].n);
+  std::vector<size_t> lvl_L(depth + 1, 0);
+  int64_t maxX = 0;
+  for (const Node& nd : nodes)
+    if (nd.child[0] >= 0) {
+      const int64_t h = nd.n / 2, h2 = nd.n - h;
+      lvl_L[nd.level] += dbytes(h * h) + dbytes(h2 * h2);
+      maxX = std::max(maxX, h * h2);
+    }
+  bytes += *std::max_element(lvl_L.begin(), lvl_L.end()) + dbytes(maxX) + 2 * dbytes(nrows * (int64_t)k) +
+           dbytes((int64_t)nodes.size() * 2 * k) + 1024;
+  char* arena = nullptr;
+  HGL_CHECK_CUDA(cudaMalloc(reinterpret_cast<void**>(&arena), bytes));
+  size_t top = 0;
+  auto take = [&](int64_t count) {
+    double* ptr = reinterpret_cast<double*>(arena + top);
+    top += dbytes(count);
+    return ptr;
+  };
+  double* T = take(trows * ldt);
+  nodes[0].out = Minv;
+  nodes[0].ldo = ldm;
+  for (size_t i = 1; i < nodes.size(); ++i) {
+    nodes[i].out = take(nodes[i].n * nodes[i].n);
+    nodes[i].ldo = nodes[i].n;
+  }
+  const size_t lbase = top;
+  top += *std::max_element(lvl_L.begin(), lvl_L.end());
+  double* X = take(maxX);
+  double* Q = take(nrows * (int64_t)k);
+  double* Qg = take(nrows * (int64_t)k);
+  double* ev = take((int64_t)nodes.size() * 2 * k);
+
   hgl_status s_ = HGL_OK;
-  double* T = cx.take(trows * ldt);
+  void* meta = nullptr;
   cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&cx.err), sizeof(int));
   if (ce == cudaSuccess) ce = cudaMemsetAsync(cx.err, 0, sizeof(int), st);
-  if (ce != cudaSuccess) s_ = cuda_error(ce, "Schur inverse setup", __FILE__, __LINE__);
-  if (s_ == HGL_OK) {
-    // one tessellation block covering the range: the block storage of the rSVD assembly
-    void* meta = nullptr;
-    ce = cudaMalloc(&meta, 64);
+  if (ce == cudaSuccess) ce = cudaMalloc(&meta, 64);
+  if (ce == cudaSuccess) {
+    // the dense Theta of the range: the rSVD's block assembly with one block [row0, row0 + nrows)
+    char hbuf[48] = {};
+    const int64_t hm[3] = {row0, 0, 0};
+    const int32_t im[3] = {(int32_t)nrows, 1, 1};
+    memcpy(hbuf, hm, 24);
+    memcpy(hbuf + 24, im, 12);
+    ce = cudaMemcpyAsync(meta, hbuf, 36, cudaMemcpyHostToDevice, st);
+    rsvd::Blocks B{};
+    B.nb = 1;
+    B.l = 1;
+    B.lpad = 16;
+    B.k = 1;
+    B.ldA = ldt;
+    B.Ktot = ldt;
+    B.v0 = static_cast<const int64_t*>(meta);
+    B.arow = B.v0 + 1;
+    B.koff = B.v0 + 2;
+    B.rows = reinterpret_cast<const int32_t*>(static_cast<char*>(meta) + 24);
+    B.lb = B.rows + 1;
+    B.kb = B.rows + 2;
     if (ce == cudaSuccess) {
-      int64_t hm[3] = {row0, 0, 0};
-      int32_t im[3] = {(int32_t)nrows, 1, 1};
-      char buf[48];
-      memcpy(buf, hm, 24);
-      memcpy(buf + 24, im, 12);
-      ce = cudaMemcpyAsync(meta, buf, 36, cudaMemcpyHostToDevice, st);
-      rsvd::Blocks B{};
-      B.nb = 1;
-      B.l = 1;
-      B.lpad = 16;
-      B.k = 1;
-      B.ldA = ldt;
-      B.Ktot = ldt;
-      B.v0 = static_cast<const int64_t*>(meta);
-      B.arow = B.v0 + 1;
-      B.koff = B.v0 + 2;
-      B.rows = reinterpret_cast<const int32_t*>(static_cast<char*>(meta) + 24);
-      B.lb = B.rows + 1;
-      B.kb = B.rows + 2;
-      if (ce == cudaSuccess) {
-        count_launch();
-        rsvd::k_assemble<double, double><<<cx.sms * 8, 256, 0, st>>>(B, trows, g->csr_ptr, g->csr_idx, g->csc_ptr,
-                                                                     g->csc_idx, g->s, g->t, T);
-        ce = cudaGetLastError();
-      }
-      if (ce == cudaSuccess) s_ = schur_rec(cx, T, ldt, nrows, row0, Minv, ldm);
-      if (ce == cudaSuccess && s_ == HGL_OK) ce = cudaStreamSynchronize(st);
-      cudaFree(meta);
+      count_launch();
+      rsvd::k_assemble<double, double><<<cx.sms * 8, 256, 0, st>>>(B, trows, g->csr_ptr, g->csr_idx, g->csc_ptr,
+                                                                   g->csc_idx, g->s, g->t, T);
+      ce = cudaGetLastError();
     }
-    if (ce != cudaSuccess && s_ == HGL_OK) s_ = cuda_error(ce, "Schur inverse", __FILE__, __LINE__);
+  }
+  if (ce != cudaSuccess) s_ = cuda_error(ce, "Schur inverse setup", __FILE__, __LINE__);
+
+  // bottom-up: per level, the Schur complements of its internal nodes (from the next
+  // level's inverses), one batch of Algorithm 1 for those and for the level's leaf
+  // blocks, then the internal nodes' off-diagonal blocks
+  for (int lv = depth; lv >= 0 && s_ == HGL_OK; --lv) {
+    std::vector<Item> items;
+    size_t ltop = lbase;
+    for (const Node& nd : nodes) {
+      if (nd.level != lv || s_ != HGL_OK) continue;
+      const double* T11 = T + nd.off * ldt + nd.off;
+      if (nd.child[0] < 0) {
+        items.push_back(Item{T11, ldt, row0 + nd.off, nd.n, nd.out, nd.ldo});
+        continue;
+      }
+      const int64_t h = nd.n / 2, h2 = nd.n - h;
+      const double* T12 = T11 + h;
+      const double* T21 = T11 + h * ldt;
+      const double* T22 = T21 + h;
+      const Node& c1 = nodes[nd.child[0]];
+      const Node& c2 = nodes[nd.child[1]];
+      double* L1 = reinterpret_cast<double*>(arena + ltop);
+      ltop += dbytes(h * h);
+      double* L2 = reinterpret_cast<double*>(arena + ltop);
+      ltop += dbytes(h2 * h2);
+      // L1 = T11 + (T12 M22^-1) T21,  L2 = T22 + (T21 M11^-1) T12
+      s_ = dense_gemm(cx, h, h2, h2, T12, ldt, c2.out, c2.ldo, false, nullptr, 0, X, h2);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h, h, h2, X, h2, T21, ldt, false, T11, ldt, L1, h);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h2, h, h, T21, ldt, c1.out, c1.ldo, false, nullptr, 0, X, h);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h2, h2, h, X, h, T12, ldt, false, T22, ldt, L2, h2);
+      items.push_back(Item{L1, h, row0 + nd.off, h, nd.out, nd.ldo});
+      items.push_back(Item{L2, h2, row0 + nd.off + h, h2, nd.out + h * nd.ldo + h, nd.ldo});
+    }
+    if (s_ == HGL_OK && !items.empty()) s_ = lowrank_inverses(cx, items, row0, Q, Qg, ev);
+    for (const Node& nd : nodes) {
+      if (nd.level != lv || nd.child[0] < 0 || s_ != HGL_OK) continue;
+      const int64_t h = nd.n / 2, h2 = nd.n - h;
+      const double* T12 = T + nd.off * ldt + nd.off + h;
+      const double* T21 = T + (nd.off + h) * ldt + nd.off;
+      const Node& c1 = nodes[nd.child[0]];
+      double* O12 = nd.out + h;
+      double* O21 = nd.out + h * nd.ldo;
+      const double* O22 = nd.out + h * nd.ldo + h;
+      // -M11^-1 M12 Z2^-1 = (M11^-1 T12) Z2^-1,  -Z2^-1 M21 M11^-1 = (Z2^-1 T21) M11^-1
+      s_ = dense_gemm(cx, h, h2, h, c1.out, c1.ldo, T12, ldt, false, nullptr, 0, X, h2);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h, h2, h2, X, h2, O22, nd.ldo, false, nullptr, 0, O12, nd.ldo);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h2, h, h2, O22, nd.ldo, T21, ldt, false, nullptr, 0, X, h);
+      if (s_ == HGL_OK) s_ = dense_gemm(cx, h2, h, h, X, h, c1.out, c1.ldo, false, nullptr, 0, O21, nd.ldo);
+    }
   }
   if (s_ == HGL_OK) {
+    ce = cudaStreamSynchronize(st);
     int e = 0;
-    ce = cudaMemcpy(&e, cx.err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (ce != cudaSuccess) s_ = cuda_error(ce, "Schur inverse status", __FILE__, __LINE__);
+    if (ce == cudaSuccess) ce = cudaMemcpy(&e, cx.err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) s_ = cuda_error(ce, "Schur inverse", __FILE__, __LINE__);
     else if (e != 0) s_ = record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
   }
   cudaStreamSynchronize(st);
+  if (meta) cudaFree(meta);
   if (cx.err) cudaFree(cx.err);
-  cudaFree(mem);
+  cudaFree(arena);
   buffer_free(cx.split);
   buffer_free(cx.rsvd);
   return s_;

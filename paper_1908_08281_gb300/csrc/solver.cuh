@@ -101,10 +101,12 @@ hgl_status precond_build(const hgl_graph* g, const double* w, double lam, const 
 
 // sum over all entries of F*F (FP64 panel), deterministic; synchronises the stream.
 hgl_status panel_norm2(const hgl_graph* g, const double* F, int64_t ldf, int c, cudaStream_t st, double* out);
-// Algorithm 1 (Rayleigh-Ritz, FP64) on the symmetric part of one dense nb x nb matrix L,
-// Omega drawn for global rows v0 ..; Ritz vectors to Qout (nb x min(k, nb)), values to ev.
-hgl_status dense_rsvd_fp64(const double* L, int64_t ldl, int64_t nb, int64_t v0, int k, int p, int q, uint64_t seed,
-                           Buffer& space, double* Qout, double* ev, int* kb_out, cudaStream_t st);
+// Algorithm 1 (Rayleigh-Ritz, FP64) on the symmetric parts of nb dense matrices at once,
+// Omega drawn for global rows v0s[b] ..; Ritz vectors to rows v0s[b] - qrow0 .. of Qout
+// (k columns), values to ev[b * k ..].
+hgl_status dense_rsvd_batch_fp64(int nb, const double* const* Ls, const int64_t* ldls, const int64_t* v0s,
+                                 const int64_t* sizes, int k, int p, int q, uint64_t seed, Buffer& space,
+                                 double* Qout, int64_t qrow0, double* ev, cudaStream_t st);
 // sum over all entries of A*B (FP64 panels), deterministic; synchronises the stream.
 hgl_status panel_inner(const hgl_graph* g, const double* A, int64_t lda, const double* B, int64_t ldb, int c,
                        cudaStream_t st, double* out);
