@@ -518,7 +518,7 @@ def main():
         return {"F_max_col_rel": float(dF.max().item()),
                 "w_rel": float((torch.linalg.norm(wa - wb) / torch.linalg.norm(wb)).item())}
 
-    fp64 = mixed_cg = loop_acc = None
+    fp64 = mixed_cg = mixed_bf16 = loop_acc = None
     if not args.no_fp64:
         f64_ms, st64, F64, w64 = timed_loop(hgl.HGL_FP64, hgl.HGL_ROUTE_CG)
         fp64 = {"ms_per_step": f64_ms, "value": 1000.0 / f64_ms, "unit": UNIT,
@@ -532,6 +532,14 @@ def main():
                     "cg_iters_per_step": float(np.mean([s.solve.iters for s in stc])),
                     "relres_max": max(s.solve.relres_max for s in stc),
                     "speedup_over_fp64": f64_ms / cg_ms}
+        bf_ms, stb, Fb, wb = timed_loop(hgl.HGL_BF16, hgl.HGL_ROUTE_BR)
+        mixed_bf16 = {"ms_per_step": bf_ms, "value": 1000.0 / bf_ms, "unit": UNIT,
+                      "route": "block rSVD preconditioned CG, BF16 panels (FP32 accumulate) with FP64-accurate "
+                               "refinement",
+                      "cg_iters_per_step": float(np.mean([s.solve.iters for s in stb])),
+                      "refinements_per_step": float(np.mean([s.solve.refinements for s in stb])),
+                      "relres_max": max(s.solve.relres_max for s in stb),
+                      "speedup_over_fp64": f64_ms / bf_ms}
         if loops_compared:
             # the loop's exact trajectory to within 3e-10 per step: FP64 CG to 1e-10,
             # eager launches, the same 20 outer iterations from w0 (untimed)
@@ -544,11 +552,11 @@ def main():
             torch.cuda.synchronize()
             loop_acc = {"reference": "FP64 CG to relres 1e-10, same 20 outer iterations from w0",
                         "mixed_br": loop_diff(F_loop, w_loop, Ft, wt), "fp64_cg": loop_diff(F64, w64, Ft, wt),
-                        "mixed_cg": loop_diff(Fc, wc, Ft, wt),
+                        "mixed_cg": loop_diff(Fc, wc, Ft, wt), "mixed_bf16_br": loop_diff(Fb, wb, Ft, wt),
                         "mixed_br_vs_fp64_cg": loop_diff(F_loop, w_loop, F64, w64),
                         "bound_F_from_tol": (1 + wl.lam) / wl.lam * TOL}
             del Ft, wt
-        del F64, w64, Fc, wc
+        del F64, w64, Fc, wc, Fb, wb
     del F_loop, w_loop
 
     cpu = None
@@ -573,6 +581,7 @@ def main():
             "e2e": e2e,
             "fp64_cg": fp64,
             "mixed_cg_route": mixed_cg,
+            "mixed_bf16_route": mixed_bf16,
             "loop_accuracy": loop_acc,
             "cpu_baseline": cpu,
             "clocks": clocks,
