@@ -520,6 +520,8 @@ hgl_status hgl_laplacian_quadratic(hgl_graph* g, const double* w, const double* 
 
 #define HGL_ROUTE_CG 0   /* plain CG solve (CG-ITH-HWEG, Section 4)                     */
 #define HGL_ROUTE_BR 1   /* CG preconditioned by the block rSVD (BR-ITH-HWEG)          */
+#define HGL_ROUTE_BCG 2  /* block CG with a shared Krylov space over groups of k      */
+                         /* columns (hgl_block_cg_solve), FP64, eager steps only       */
 
 #define HGL_STEP_GRAPH      1 /* replay the step as one captured CUDA graph            */
 #define HGL_STEP_ACTIVE_SET 2 /* weight step by hgl_active_set_step instead of the     */
@@ -529,11 +531,12 @@ typedef struct {
   double  lam;           /* ranking regulariser (theta of Eq. 3), > 0                     */
   double  mu;            /* weight regulariser (kappa of Eq. 4), >= 0                     */
   double  eta;           /* step size of the projected gradient step                     */
-  int32_t route;         /* HGL_ROUTE_CG or HGL_ROUTE_BR                                 */
+  int32_t route;         /* HGL_ROUTE_CG, HGL_ROUTE_BR or HGL_ROUTE_BCG                  */
   int32_t flags;         /* HGL_STEP_GRAPH                                               */
   hgl_solve_opts solve;  /* inner solve options (warm start from F is always used)       */
   const int64_t* block_ptr; int32_t nblocks;   /* HGL_ROUTE_BR: host block boundaries     */
-  int32_t k, p, q;       /* HGL_ROUTE_BR: rank, oversampling, iterations                  */
+  int32_t k, p, q;       /* HGL_ROUTE_BR: rank, oversampling, iterations;                 */
+                         /* HGL_ROUTE_BCG: k = columns per group (1 .. 32)                */
   uint64_t seed;         /* HGL_ROUTE_BR: Omega seed                                      */
 } hgl_step_opts;
 

@@ -87,8 +87,32 @@ hgl_status adaptive_step_eager(hgl_graph* g, double* w, const hgl_step_opts& o, 
   so.flags |= HGL_SOLVE_WARM_START;
   hgl_solve_stats ss{};
   SolveExtras ext;
-  hgl_status solve_status = cg_solve_impl(g, w, o.lam, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true,
-                                          &ext);
+  hgl_status solve_status = HGL_OK;
+  if (o.route == HGL_ROUTE_BCG) {
+    // block CG over groups of k columns (FP64); per-group iterations and per-column
+    // relres come back through a small device buffer
+    const int G = (c + o.k - 1) / o.k;
+    void* sbuf = nullptr;
+    HGL_CHECK_CUDA(cudaMalloc(&sbuf, sizeof(double) * c + sizeof(int32_t) * G));
+    double* d_rel = static_cast<double*>(sbuf);
+    int32_t* d_it = reinterpret_cast<int32_t*>(d_rel + c);
+    solve_status = hgl_block_cg_solve(g, w, o.lam, Y, ldy, F, ldf, c, o.k, so.tol > 0 ? so.tol : 1e-10,
+                                      so.max_iter > 0 ? so.max_iter : 1000, HGL_SOLVE_WARM_START, d_rel, d_it, st);
+    std::vector<double> rel(c);
+    std::vector<int32_t> its(G);
+    cudaError_t ce = cudaMemcpy(rel.data(), d_rel, sizeof(double) * c, cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess) ce = cudaMemcpy(its.data(), d_it, sizeof(int32_t) * G, cudaMemcpyDeviceToHost);
+    cudaFree(sbuf);
+    if (ce != cudaSuccess) return cuda_error(ce, "block CG statistics", __FILE__, __LINE__);
+    ss.status = solve_status;
+    for (int j = 0; j < c; ++j) {
+      ss.relres_max = std::max(ss.relres_max, rel[j]);
+      ss.converged += rel[j] <= so.tol ? 1 : 0;
+    }
+    for (int i = 0; i < G; ++i) ss.iters = std::max(ss.iters, its[i]);
+  } else {
+    solve_status = cg_solve_impl(g, w, o.lam, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true, &ext);
+  }
   if (P) hgl_precond_destroy(P);
   if (solve_status != HGL_OK && solve_status != HGL_ERR_NOT_CONVERGED) return solve_status;
 
@@ -352,6 +376,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
   if (!(o.flags & HGL_STEP_GRAPH)) return adaptive_step_eager(g, w, o, Y, ldy, F, ldf, c, stats, st);
   if (o.solve.dtype != HGL_FP64 && o.solve.dtype != HGL_FP32 && o.solve.dtype != HGL_BF16)
     return record_error(HGL_ERR_INVALID_ARG, "unknown solve dtype");
+  if (o.route == HGL_ROUTE_BCG) return record_error(HGL_ERR_INVALID_ARG, "the block CG route runs eagerly");
   StepGraph*& sg = g->step_graph;
   if (!sg || !sg->matches(w, o, Y, ldy, F, ldf, c)) {
     // a new call pattern: run it eagerly (which also sizes every work buffer the graph
@@ -416,8 +441,10 @@ extern "C" hgl_status hgl_adaptive_step(hgl_graph* g, double* w, const hgl_step_
   if (c < 1) return hgl::record_error(HGL_ERR_INVALID_ARG, "c must be >= 1");
   if (!(opts->lam > 0.0) || opts->mu < 0.0 || !(opts->eta >= 0.0))
     return hgl::record_error(HGL_ERR_INVALID_ARG, "need lam > 0, mu >= 0, eta >= 0");
-  if (opts->route != HGL_ROUTE_CG && opts->route != HGL_ROUTE_BR)
+  if (opts->route != HGL_ROUTE_CG && opts->route != HGL_ROUTE_BR && opts->route != HGL_ROUTE_BCG)
     return hgl::record_error(HGL_ERR_INVALID_ARG, "unknown route");
+  if (opts->route == HGL_ROUTE_BCG && opts->solve.dtype != HGL_FP64)
+    return hgl::record_error(HGL_ERR_INVALID_ARG, "the block CG route is FP64");
   HGL_TRY(hgl::check_panel(Y, ldy, c, 8, "Y"));
   HGL_TRY(hgl::check_panel(F, ldf, c, 8, "F"));
   return hgl::adaptive_step_impl(g, w, *opts, Y, ldy, F, ldf, c, stats, hgl::as_stream(stream));

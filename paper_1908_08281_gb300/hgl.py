@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "hgl.h")
 HGL_FP64, HGL_FP32, HGL_BF16 = 0, 1, 2
 HGL_SOLVE_WARM_START = 1
 HGL_GRAD_DV_FROZEN = 1
-HGL_ROUTE_CG, HGL_ROUTE_BR = 0, 1
+HGL_ROUTE_CG, HGL_ROUTE_BR, HGL_ROUTE_BCG = 0, 1, 2
 HGL_STEP_GRAPH = 1
 HGL_STEP_ACTIVE_SET = 2
 

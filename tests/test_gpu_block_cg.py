@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import synth
-from oracle.core import block_cg_solve, cg_solve, solve_dense
+from oracle.core import adaptive_loop, block_cg_solve, cg_solve, solve_dense
 from oracle.incidence import build_incidence, incidence_matrix
 from paper_1908_08281_gb300 import build as _build
 from paper_1908_08281_gb300 import hgl
@@ -139,3 +139,26 @@ def test_block_cg_argument_errors():
     for s in (0, 33):
         with pytest.raises(hgl.HglError):
             hgl.block_cg_solve(g, wt, 0.5, _panel(Y), s)
+
+
+def test_adaptive_step_block_cg_route_matches_oracle_loop():
+    """hgl_adaptive_step with HGL_ROUTE_BCG (block CG over groups of k = 4 columns,
+    warm-started from the previous F) through two outer iterations of the small workload
+    against the oracle's loop (FP64 CG to 1e-12): F and w to 1e-8."""
+    wl = synth.WORKLOADS["small_fp64"]
+    d = synth.make_hypergraph(wl, 13)
+    H, g = _graph(d["n"], d["m"], d["edge_ptr"], d["members"])
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    F.zero_()
+    for _ in range(2):
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, wl.mu, wl.eta, tol=1e-11, route=hgl.HGL_ROUTE_BCG, k=4)
+        assert st.solve.relres_max <= 1e-11 and st.solve.iters > 0
+    Fr, wr, _ = adaptive_loop(H, d["w0"], wl.lam, wl.mu, wl.eta, d["Y"], 2, tol=1e-12)
+    err = np.linalg.norm(F.cpu().numpy() - Fr, axis=0) / np.linalg.norm(Fr, axis=0)
+    assert err.max() <= 1e-8
+    assert np.linalg.norm(wt.cpu().numpy() - wr) / np.linalg.norm(wr) <= 1e-8
+    with pytest.raises(hgl.HglError):
+        hgl.adaptive_step(g, wt, Y, F, wl.lam, wl.mu, wl.eta, tol=1e-11, route=hgl.HGL_ROUTE_BCG, k=4,
+                          flags=hgl.HGL_STEP_GRAPH)
