@@ -50,6 +50,7 @@ SEED = 20190822
 NCU_TRAFFIC_PER_LAUNCH = {("operator", 128): 66.0e9, ("residual", 128): 149.2e9}
 LOOP = 20           # outer iterations of one adaptive loop
 K_RANK, P_OVER, Q_ITERS = 64, 10, 2
+BCG_S, BCG_STEPS = 32, 4   # block CG comparator: columns per group, outer iterations timed
 
 
 def parse():
@@ -65,6 +66,8 @@ def parse():
     ap.add_argument("--eta", type=float, default=None, help="override the workload's step size")
     ap.add_argument("--no-tune", action="store_true", help="keep the default column chunks (no autotuning)")
     ap.add_argument("--no-graph", action="store_true", help="run each outer iteration eagerly (no CUDA graph)")
+    ap.add_argument("--schur", default=None,
+                    help="time the nested Schur-complement inverse at these vertex counts (comma list) and exit")
     return ap.parse_args()
 
 
@@ -308,11 +311,50 @@ def config_dict(d, bp):
             "l2_flush": "inputs larger than L2 (>= 2 GB panels)"}
 
 
+def run_schur(sizes):
+    """The nested 2 x 2 Schur-complement inverse (Eqs. 12-14) at the paper's scale: a
+    hypergraph of n vertices and 1.5 n hyperedges of U{2..20} members, r_min = k = 50,
+    p = 10, q = 2; the dense products on tcgen05 (3xTF32) and on FP64 CUDA cores.  One
+    JSON line per size."""
+    import torch
+
+    from paper_1908_08281_gb300 import build as _build
+    from paper_1908_08281_gb300 import hgl
+    _build.build()
+    hgl.lib()
+    wl = synth.WORKLOADS["small_fp64"]
+    for n in sizes:
+        d = synth.make_hypergraph(wl, 3, n=n, m=int(1.5 * n), c=1)
+        g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
+        w = torch.full((d["m"],), 1.0 / d["m"], dtype=torch.float64, device="cuda")
+        line = {"measurement": "nested Schur-complement inverse", "n": n, "m": d["m"], "r_min": 50, "k": 50,
+                "p": 10, "q": 2}
+        for dt, name in ((hgl.HGL_FP32, "tcgen05_3xtf32"), (hgl.HGL_FP64, "fp64_cuda_cores")):
+            hgl.schur_inverse(g, w, 0.5, 0, n, 50, 50, 10, 2, 1, dt)
+            torch.cuda.synchronize()
+            hgl.profile_enable(True)
+            t0 = time.perf_counter()
+            hgl.schur_inverse(g, w, 0.5, 0, n, 50, 50, 10, 2, 1, dt)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            ms, cnt = hgl.profile_read(hgl.PROF_SCHUR_GEMM)
+            gm, gc = hgl.profile_read(hgl.PROF_GEMM)
+            hgl.profile_enable(False)
+            line[name] = {"seconds": t, "dense_products_ms": ms, "dense_product_launches": cnt,
+                          "useful_TFLOPs": 2.67 * 2.0 * float(n) ** 3 / (ms / 1e3) / 1e12,
+                          "algorithm1_products_ms": gm}
+        print(json.dumps(line), flush=True)
+        g.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.schur:
+        run_schur([int(x) for x in args.schur.split(",")])
         return
     import torch
     import torch.distributed as dist
@@ -518,7 +560,7 @@ def main():
         return {"F_max_col_rel": float(dF.max().item()),
                 "w_rel": float((torch.linalg.norm(wa - wb) / torch.linalg.norm(wb)).item())}
 
-    fp64 = mixed_cg = mixed_bf16 = loop_acc = None
+    fp64 = mixed_cg = mixed_bf16 = fp64_bcg = loop_acc = None
     if not args.no_fp64:
         f64_ms, st64, F64, w64 = timed_loop(hgl.HGL_FP64, hgl.HGL_ROUTE_CG)
         fp64 = {"ms_per_step": f64_ms, "value": 1000.0 / f64_ms, "unit": UNIT,
@@ -532,6 +574,28 @@ def main():
                     "cg_iters_per_step": float(np.mean([s.solve.iters for s in stc])),
                     "relres_max": max(s.solve.relres_max for s in stc),
                     "speedup_over_fp64": f64_ms / cg_ms}
+        # O'Leary's block CG (FP64, groups of 32 columns, eager launches: its host
+        # synchronisations per iteration keep it out of a captured graph), timed on the
+        # first BCG_STEPS outer iterations of the same loop
+        Fk = hgl.padded_panel(n, c, torch.float64, dev)
+        Fk.zero_()
+        wk = w0.clone()
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        stk = [hgl.adaptive_step(g, wk, Y, Fk, lam=wl.lam, mu=wl.mu, eta=eta, tol=TOL, dtype=hgl.HGL_FP64,
+                                 route=hgl.HGL_ROUTE_BCG, k=BCG_S) for _ in range(BCG_STEPS)]
+        k1.record(stream)
+        torch.cuda.synchronize()
+        bcg_ms = k0.elapsed_time(k1) / BCG_STEPS
+        f64_cg_first = float(np.mean([s.solve.iters for s in st64[:BCG_STEPS]]))
+        fp64_bcg = {"ms_per_step": bcg_ms, "value": 1000.0 / bcg_ms, "unit": UNIT,
+                    "route": f"block CG (O'Leary), FP64, groups of {BCG_S} columns, eager launches",
+                    "steps_timed": BCG_STEPS, "iters_per_step": float(np.mean([s.solve.iters for s in stk])),
+                    "fp64_cg_iters_same_steps": f64_cg_first,
+                    "relres_max": max(s.solve.relres_max for s in stk)}
+        del Fk, wk
         bf_ms, stb, Fb, wb = timed_loop(hgl.HGL_BF16, hgl.HGL_ROUTE_BR)
         mixed_bf16 = {"ms_per_step": bf_ms, "value": 1000.0 / bf_ms, "unit": UNIT,
                       "route": "block rSVD preconditioned CG, BF16 panels (FP32 accumulate) with FP64-accurate "
@@ -582,6 +646,7 @@ def main():
             "fp64_cg": fp64,
             "mixed_cg_route": mixed_cg,
             "mixed_bf16_route": mixed_bf16,
+            "fp64_block_cg": fp64_bcg,
             "loop_accuracy": loop_acc,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -2,7 +2,8 @@
 allocates nothing in the call (for callers whose device memory all comes from their
 own pool or budget, or that cannot take the synchronisation of cudaMalloc/cudaFree)
 must give the same Z as hgl_apply_theta, on two calls in a row that share its fixed
-scratch array.  This file is named to be collected last."""
+scratch array, and for FP64 panels the oracle's Z = a X + b Theta X (Eq. 1).  This
+file is named to be collected last."""
 import ctypes
 
 import numpy as np
@@ -10,6 +11,7 @@ import pytest
 import torch
 
 import synth
+from oracle import core, incidence
 from paper_1908_08281_gb300 import build as _build
 from paper_1908_08281_gb300 import hgl
 
@@ -45,6 +47,10 @@ def test_noalloc_matches_allocating_entry_point(lib, dtype, c, m):
     assert _raw_call(lib, lib.hgl_apply_theta, g, w, X, Zref, 1.5, -1.0) == 0
     ref = Zref.to(torch.float64).cpu().numpy()
     tol = {torch.float64: 1e-12, torch.float32: 1e-5, torch.bfloat16: 2e-2}[dtype]
+    if dtype == torch.float64:
+        H = incidence.incidence_matrix(incidence.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"]))
+        ora = core.theta_apply(H, w.cpu().numpy(), X.cpu().numpy(), 1.5, -1.0)
+        assert np.abs(ref - ora).max() <= tol * np.abs(ora).max()
     for call in range(2):
         Z = hgl.padded_panel(d["n"], c, dtype, dev, fill=float("nan"))
         st = _raw_call(lib, lib.hgl_apply_theta_noalloc, g, w, X, Z, 1.5, -1.0)
@@ -53,6 +59,8 @@ def test_noalloc_matches_allocating_entry_point(lib, dtype, c, m):
         out = Z.to(torch.float64).cpu().numpy()
         scale = np.abs(ref).max()
         assert np.abs(out - ref).max() <= tol * scale, (call, np.abs(out - ref).max() / scale)
+        if dtype == torch.float64:
+            assert np.abs(out - ora).max() <= tol * np.abs(ora).max(), call
     g.close()
 
 
