@@ -389,8 +389,12 @@ def main():
         op32, pair32, grid32 = hgl.tune_operator(g, w0, c, hgl.HGL_FP32)
         op64, _, grid64 = hgl.tune_operator(g, w0, c, hgl.HGL_FP64)
         policy = ("one wave", "eight per SM")
+        broute, b_dense, b_sparse = hgl.tune_block_rsvd(g, w0, bp, K_RANK, P_OVER, Q_ITERS)
         tuned = {"operator_chunk_fp32": op32, "residual_chunk": pair32, "operator_chunk_fp64": op64,
-                 "grid_fp32": policy[grid32], "grid_fp64": policy[grid64], "tune_s": time.time() - t0}
+                 "grid_fp32": policy[grid32], "grid_fp64": policy[grid64],
+                 "block_products": {"route": "sparse" if broute == hgl.HGL_BLOCKS_SPARSE else "dense (tcgen05)",
+                                    "ms_per_build_dense": b_dense, "ms_per_build_sparse": b_sparse},
+                 "tune_s": time.time() - t0}
 
     def reset():
         w.copy_(w0)

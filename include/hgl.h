@@ -354,6 +354,24 @@ hgl_status hgl_block_rsvd(const hgl_graph* g, const double* w, double lam,
 hgl_status hgl_set_block_product(hgl_graph* g, int32_t mode);
 
 /*
+ * hgl_tune_block_rsvd -- choose the route of the BF16 block rSVD's products Theta_bb S
+ * (Section 3, Algorithm 1) for these blocks by timing both on this graph: the dense
+ * route (assembly of the dense BF16 blocks + 2q + 2 tcgen05 products) against the
+ * sparse route (2q + 2 products from the incidence lists), each after a warm-up, CUDA
+ * events on `stream`.  The faster becomes the graph's hgl_set_block_product setting
+ * (HGL_BLOCKS_DENSE or HGL_BLOCKS_SPARSE).  The paper has no counterpart: which route
+ * is faster depends on how much of Theta the diagonal blocks hold.
+ *   w            device FP64[m] (sets the degree vectors)
+ *   block_ptr    host int64[nblocks + 1], 0 .. n;  k, p, q as for hgl_block_rsvd
+ *   route        optional host out: the chosen setting
+ *   ms_dense, ms_sparse  optional host out: the measured times of one build's products
+ * Allocates and frees its work space.  Synchronises `stream`.
+ */
+hgl_status hgl_tune_block_rsvd(hgl_graph* g, const double* w, const int64_t* block_ptr, int32_t nblocks,
+                               int32_t k, int32_t p, int32_t q, int32_t* route, double* ms_dense,
+                               double* ms_sparse, void* stream);
+
+/*
  * hgl_block_product -- D_b = Theta_bb S_b for every diagonal tessellation block b, the
  * product that each step of Algorithm 1 (Section 3) applies to the block's basis,
  * computed as the BF16 block rSVD computes it: the tcgen05 grouped GEMM over the dense

@@ -788,3 +788,73 @@ hgl_status dense_rsvd_batch_fp64(int nb, const double* const* Ls, const int64_t*
 }
 
 }  // namespace hgl
+
+// Route of the BF16 build's products, chosen by timing them on this graph: the dense
+// route costs one assembly of the dense BF16 blocks plus 2q + 2 tcgen05 products, the
+// sparse route 2q + 2 products from the incidence lists.  Each is timed (CUDA events)
+// after a warm-up; the faster becomes the graph's block-product setting.  Synchronous.
+extern "C" hgl_status hgl_tune_block_rsvd(hgl_graph* g, const double* w, const int64_t* block_ptr, int32_t nblocks,
+                                          int32_t k, int32_t p, int32_t q, int32_t* route, double* ms_dense,
+                                          double* ms_sparse, void* stream) {
+  using namespace hgl;
+  if (!g || !w) return record_error(HGL_ERR_INVALID_ARG, "graph or w is NULL");
+  HGL_TRY(precond_validate(g, block_ptr, nblocks, k, p, q, HGL_BF16));
+  cudaStream_t st = as_stream(stream);
+  HGL_TRY(degrees_launch(g, w, st));
+  const int l = k + p;
+  const int lpad = (int)rup(l, 16);
+  const int sms = g->num_sms;
+  const int nprod = 2 * q + 2;
+  double ms[2] = {0.0, 0.0};
+  Buffer space;
+  hgl_status s_ = HGL_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HGL_CHECK_CUDA(cudaEventCreate(&e0));
+  HGL_CHECK_CUDA(cudaEventCreate(&e1));
+  for (int sparse = 0; sparse < 2 && s_ == HGL_OK; ++sparse) {
+    Work wk;
+    s_ = plan(g, space, block_ptr, nblocks, k, l, lpad, HGL_BF16, sparse != 0, &wk);
+    if (s_ != HGL_OK) break;
+    auto once = [&]() -> hgl_status {
+      HGL_CHECK_CUDA(cudaMemsetAsync(wk.fail, 0, 8, st));
+      HGL_LPAD_SWITCH(lpad, {
+        if (sparse) {
+          hgl::count_launch();
+          rsvd::k_omega_rows<LP><<<sms * 8, 256, 0, st>>>(wk.B, wk.rows_tot, 1, nullptr, static_cast<float*>(wk.Qf));
+        } else {
+          hgl::count_launch(2);
+          rsvd::k_assemble<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
+              wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->s32, g->t32,
+              static_cast<__nv_bfloat16*>(wk.A));
+          rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, 1, nullptr, static_cast<__nv_bfloat16*>(wk.St));
+        }
+        HGL_CHECK_CUDA(cudaGetLastError());
+        for (int i = 0; i < nprod; ++i) HGL_TRY(gemm<LP>(g, wk, HGL_BF16, sms, st));
+      });
+      return HGL_OK;
+    };
+    s_ = once();  // warm-up
+    if (s_ != HGL_OK) break;
+    HGL_CHECK_CUDA(cudaEventRecord(e0, st));
+    s_ = once();
+    if (s_ != HGL_OK) break;
+    HGL_CHECK_CUDA(cudaEventRecord(e1, st));
+    HGL_CHECK_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    HGL_CHECK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    ms[sparse] = t;
+    int32_t flags[2] = {0, 0};
+    HGL_CHECK_CUDA(cudaMemcpy(flags, wk.fail, 8, cudaMemcpyDeviceToHost));
+    if (flags[1] != 0) s_ = record_error(HGL_ERR_TIMEOUT, "the tensor-core GEMM hit its wait limit");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  buffer_free(space);
+  HGL_TRY(s_);
+  g->block_product = ms[1] < ms[0] ? HGL_BLOCKS_SPARSE : HGL_BLOCKS_DENSE;
+  if (route) *route = g->block_product;
+  if (ms_dense) *ms_dense = ms[0];
+  if (ms_sparse) *ms_sparse = ms[1];
+  return HGL_OK;
+}

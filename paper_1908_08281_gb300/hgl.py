@@ -92,6 +92,8 @@ _SIGNATURES = {
     "hgl_set_block_product": (_I32, [_P, _I32]),
     "hgl_block_product": (_I32, [_P, _P, ctypes.POINTER(_I64), _I32, _I32, _P, _I64, _P, _I64, _P]),
     "hgl_schur_inverse": (_I32, [_P, _P, _D, _I64, _I64, _I32, _I32, _I32, _I32, _U64, _I32, _P, _I64, _P]),
+    "hgl_tune_block_rsvd": (_I32, [_P, _P, ctypes.POINTER(_I64), _I32, _I32, _I32, _I32, ctypes.POINTER(_I32),
+                                   ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
     "hgl_block_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
@@ -424,6 +426,16 @@ def schur_inverse(g: Graph, w: torch.Tensor, lam: float, row0: int, nrows: int, 
     _check(lib().hgl_schur_inverse(g.handle, _vec(w, "w"), lam, row0, nrows, r_min, k, p, q, seed, dtype,
                                    ctypes.c_void_p(out.data_ptr()), nrows, _stream(stream)))
     return out
+
+
+def tune_block_rsvd(g: Graph, w: torch.Tensor, block_ptr, k: int, p: int, q: int, stream=None):
+    """Time the block rSVD's product routes on this graph and keep the faster;
+    returns (route, ms_dense, ms_sparse)."""
+    bp = (ctypes.c_int64 * len(block_ptr))(*[int(x) for x in block_ptr])
+    route, md, ms = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().hgl_tune_block_rsvd(g.handle, _vec(w, "w"), bp, len(block_ptr) - 1, k, p, q, ctypes.byref(route),
+                                     ctypes.byref(md), ctypes.byref(ms), _stream(stream)))
+    return route.value, md.value, ms.value
 
 
 def selftest_wait_timeout(limit_cycles: int, stream=None):

@@ -82,6 +82,28 @@ def test_block_product_route_by_fill():
         hgl.set_block_product(g, 7)
 
 
+def test_tune_block_rsvd_keeps_the_faster_route():
+    """hgl_tune_block_rsvd times both product routes for the blocks and sets the faster
+    one: later builds take it, and the factors still match the FP64 route's."""
+    rng = np.random.default_rng(17)
+    n, m = 40000, 60000
+    mem = np.sort(np.stack([rng.choice(n, 3, replace=False) for _ in range(m)]), axis=1).ravel()
+    g = hgl.build_incidence(n, m, np.arange(0, 3 * m + 1, 3, dtype=np.int64), mem.astype(np.int32))
+    wt = torch.full((m,), 1.0 / m, dtype=torch.float64, device=DEV)
+    bp = [0, 10000, 20000, 30000, 40000]
+    route, md, ms = hgl.tune_block_rsvd(g, wt, bp, 8, 4, 1)
+    assert md > 0 and ms > 0
+    assert route == (hgl.HGL_BLOCKS_SPARSE if ms < md else hgl.HGL_BLOCKS_DENSE)
+    gemm, spmm = _route_used(g, wt, bp)
+    assert (spmm > 0) == (route == hgl.HGL_BLOCKS_SPARSE) and (gemm > 0) == (route == hgl.HGL_BLOCKS_DENSE)
+    P16 = hgl.block_rsvd(g, wt, 0.5, bp, 8, 4, 1, SEED, gemm_dtype=hgl.HGL_BF16)
+    P64 = hgl.block_rsvd(g, wt, 0.5, bp, 8, 4, 1, SEED, gemm_dtype=hgl.HGL_FP64)
+    for b in range(len(bp) - 1):
+        e16 = hgl.precond_export(P16, b)[1].cpu().numpy()
+        e64 = hgl.precond_export(P64, b)[1].cpu().numpy()
+        assert np.abs(e16 - e64).max() <= 3e-2 * e64.max()
+
+
 def test_rsvd_fp64_matches_oracle():
     wl, d, H, w, g = _setup()
     bp = d["block_ptr"]
