@@ -285,6 +285,7 @@ void hgl_graph_destroy(hgl_graph* g) {
   hgl::buffer_free(g->misc);
   hgl::buffer_free(g->step);
   hgl::buffer_free(g->rsvd);
+  hgl::buffer_free(g->edge_tf);
   delete g;
 }
 

@@ -420,7 +420,8 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
   auto residual = [&](const int32_t* guard) -> hgl_status {
     int rr_rows = 0;
     HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0, gy,
-                        c, R32, sm.pa, st, &rr_rows, guard));
+                        c, R32, sm.pa, st, &rr_rows, guard, extras ? extras->edge_tf : nullptr,
+                        extras ? extras->edge_ldtf : 0, extras ? extras->edge_ex : nullptr));
     CgState Sg = S;
     Sg.guard = guard;
     return cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, Sg, st);

@@ -74,7 +74,8 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
        const int32_t* __restrict__ order, int64_t nheavy, const float* __restrict__ s_hi,
        const float* __restrict__ s_lo, const float* __restrict__ t_hi, const float* __restrict__ t_lo,
        const float* __restrict__ Fh, const float* __restrict__ Fl, int64_t ldf, int c0, int cw,
-       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt, const int32_t* __restrict__ guard) {
+       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt, const int32_t* __restrict__ guard,
+       float* __restrict__ tf, int64_t ldtf, double* __restrict__ ex) {
   if (guard && *guard == 0) return;
   constexpr int E = 4, G = 32 / LG, WARPS = THREADS / 32, TILE = LG * NV * E;
   const int lane = threadIdx.x & 31, grp = lane / LG, l = lane % LG, wid = threadIdx.x >> 5;
@@ -139,6 +140,7 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
     }
     if (grp == 0) {
       const f2 te{t_hi[e], t_lo[e]};
+      double d = 0.0;  // sum of sigma^2 over this lane's columns (for the gradient)
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const int col = (k * LG + l) * E;
@@ -149,10 +151,19 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
             const f2 r = mul2(te, acc[k][j]);
             oh[j] = r.hi;
             ol[j] = r.lo;
+            d += (double)acc[k][j].hi * (double)acc[k][j].hi;
           }
           vstore<float, float, E>(Th + e * ldt + col, oh, E);
           vstore<float, float, E>(Tl + e * ldt + col, ol, E);
+          // the gradient's t * sigma in FP32, full width, at the residual's (final) F
+          if (tf) vstore<float, float, E>(tf + e * ldtf + c0 + col, oh, E);
         }
+      }
+      if (ex) {
+        const unsigned gmask = LG == 32 ? 0xffffffffu : ((1u << LG) - 1u);
+#pragma unroll
+        for (int off = 1; off < LG; off <<= 1) d += __shfl_xor_sync(gmask, d, off);
+        if (l == 0) ex[e] = (c0 == 0 ? 0.0 : ex[e]) + d;
       }
     }
   }

@@ -107,6 +107,7 @@ struct hgl_graph {
   hgl::Buffer misc;            // gradient vectors (ex[m], phi[n])
   hgl::Buffer step;            // adaptive-step vectors (grad, w_old, projection work)
   hgl::Buffer rsvd;            // block rSVD work space (dense blocks, bases, Grams)
+  hgl::Buffer edge_tf;         // m x c FP32 t * (H^T s F) from the pair residual, for the gradient
   int block_product = HGL_BLOCKS_AUTO;  // route of the rSVD's products Theta_bb S
   int chunk_cols = 0;          // operator column chunk (0 = library default)
   // hyperedges in decreasing size order; the first nheavy (size > HEAVY_ROW) are

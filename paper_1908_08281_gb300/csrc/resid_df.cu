@@ -36,7 +36,7 @@ hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf
 hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
                        const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
                        double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows,
-                       const int32_t* guard) {
+                       const int32_t* guard, float* tf, int64_t ldtf, double* ex) {
   constexpr int E = 4;
   const int nvec = (c + E - 1) / E;
   int lg = 1, nv = 1;
@@ -67,7 +67,7 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
     grid2 = grid_vertex(reinterpret_cast<const void*>(df::k_vertex<LG_, NV_>));                                    \
     df::k_edge<LG_, NV_><<<grid1, df::THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->edge_order, g->nheavy,   \
                                                         s_hi, s_lo, t_hi, t_lo, Fh, Fl, ld32, c0, cw, Th, Tl,    \
-                                                        (int64_t)cc, guard);                                     \
+                                                        (int64_t)cc, guard, tf, ldtf, ex);                       \
     df::k_vertex<LG_, NV_><<<grid2, df::THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, s_hi, s_lo, Th, Tl,     \
                                                           (int64_t)cc, Fh, Fl, ld32, Y, ldy, a, b, gy, c0, cw, c, \
                                                           R, ld32, partials, guard);                              \

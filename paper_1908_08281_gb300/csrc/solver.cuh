@@ -40,6 +40,13 @@ struct SolveExtras {
   int64_t ld32 = 0;
   // out: the per-column device state (relres, iterations, breakdown flags)
   CgState state{};
+  // in (mixed modes, optional): every pair residual also writes t * (H^T s F) in FP32
+  // to edge_tf (m x c, row stride edge_ldtf) and per hyperedge the sum of squares of
+  // H^T s F over the columns to edge_ex -- the weight gradient's first pass at the
+  // solve's final F (the last residual of a solve is taken at the returned F)
+  float* edge_tf = nullptr;
+  int64_t edge_ldtf = 0;
+  double* edge_ex = nullptr;
   // in: > 0 selects capture mode -- a fixed launch sequence without host reads (one
   // refinement sweep in mixed modes, this many CG iterations with device-side early
   // exit); the caller reads the statistics after running it (fill_stats on `state`)
@@ -58,7 +65,8 @@ hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf
 hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
                        const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
                        double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows,
-                       const int32_t* guard = nullptr);
+                       const int32_t* guard = nullptr, float* tf = nullptr, int64_t ldtf = 0,
+                       double* ex = nullptr);
 
 hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
 
@@ -72,6 +80,13 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
 
 int cg_iteration_bound(double lam, double tol);
 
+// The same gradient (Zb = F, FP32 panel) from a first pass already done: TF = t * (H^T s F)
+// (m x c FP32, row stride ldtf) and ex[e] = ||(H^T s F)_e||^2 in the graph's gradient
+// vectors (as a pair residual with SolveExtras::edge_tf writes them).
+hgl_status weight_grad_from_edges(hgl_graph* g, const double* w, const float* TF, int64_t ldtf, const float* F,
+                                  int64_t ld, int c, double mu, int flags, double* grad, cudaStream_t st);
+// The graph's gradient vectors (ex[m], phi[n]); allocates on first use.
+double* grad_vectors(hgl_graph* g, hgl_status* st);
 // grad = -theta_sign * d tr(Zb^T Theta F)/dw + 2 mu w (Zb = NULL: Zb = F), at fixed panels.
 hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
                               int dtype, double mu, int flags, double* grad, cudaStream_t st,

@@ -29,6 +29,32 @@ namespace {
 
 constexpr int RED_THREADS = 256;
 
+// Mixed-precision solves hand the weight gradient its first pass: the pair residual at
+// the final F writes t * (H^T s F) and the per-hyperedge sums of squares (graph
+// buffers, sized here on the eager call and reused by the captured one).
+hgl_status request_edges(hgl_graph* g, int c, SolveExtras* ext) {
+  hgl_status stt = HGL_OK;
+  const int64_t ld = (c + 3) / 4 * 4;
+  float* tf = static_cast<float*>(buffer_get(g->edge_tf, sizeof(float) * (size_t)g->m * ld, &stt));
+  if (!tf) return stt;
+  double* gv = grad_vectors(g, &stt);
+  if (!gv) return stt;
+  ext->edge_tf = tf;
+  ext->edge_ldtf = ld;
+  ext->edge_ex = gv;
+  return HGL_OK;
+}
+
+// The gradient at the solve's F: from the pair residual's first pass in mixed modes,
+// else from F itself.
+hgl_status step_gradient(hgl_graph* g, const double* w, const SolveExtras& ext, const double* F, int64_t ldf, int c,
+                         double mu, double* grad, cudaStream_t st) {
+  if (ext.f32 && ext.edge_tf)
+    return weight_grad_from_edges(g, w, ext.edge_tf, ext.edge_ldtf, ext.f32, ext.ld32, c, mu, 0, grad, st);
+  if (ext.f32) return weight_grad_launch(g, w, ext.f32, nullptr, ext.ld32, c, HGL_FP32, mu, 0, grad, st);
+  return weight_grad_launch(g, w, F, nullptr, ldf, c, HGL_FP64, mu, 0, grad, st);
+}
+
 // partial sums of sum_e t_e ex_e (tr F^T Theta F), ||w||^2 and ||w - w_old||^2
 __global__ void k_step_sums(int64_t m, const double* __restrict__ t, const double* __restrict__ ex,
                             const double* __restrict__ w_old, const double* __restrict__ w_new,
@@ -111,17 +137,21 @@ hgl_status adaptive_step_eager(hgl_graph* g, double* w, const hgl_step_opts& o, 
     }
     for (int i = 0; i < G; ++i) ss.iters = std::max(ss.iters, its[i]);
   } else {
+    if (so.dtype != HGL_FP64) {
+      const hgl_status er = request_edges(g, c, &ext);
+      if (er != HGL_OK) {
+        if (P) hgl_precond_destroy(P);
+        return er;
+      }
+    }
     solve_status = cg_solve_impl(g, w, o.lam, o.lam, Y, ldy, F, ldf, c, P, so, nullptr, nullptr, &ss, st, true, &ext);
   }
   if (P) hgl_precond_destroy(P);
   if (solve_status != HGL_OK && solve_status != HGL_ERR_NOT_CONVERGED) return solve_status;
 
-  // gradient at the solve's F (degrees are still those of the current w)
-  // mixed modes differentiate at the FP32 high part of F (FP32 arithmetic); FP64 mode at F
-  if (ext.f32)
-    HGL_TRY(weight_grad_launch(g, w, ext.f32, nullptr, ext.ld32, c, HGL_FP32, o.mu, 0, grad, st));
-  else
-    HGL_TRY(weight_grad_launch(g, w, F, nullptr, ldf, c, HGL_FP64, o.mu, 0, grad, st));
+  // gradient at the solve's F (degrees are still those of the current w): mixed modes
+  // at F's pair through the last pair residual's first pass, FP64 mode at F
+  HGL_TRY(step_gradient(g, w, ext, F, ldf, c, o.mu, grad, st));
   // ||F||^2 for the objective
   HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   if (o.flags & HGL_STEP_ACTIVE_SET)
@@ -255,12 +285,10 @@ hgl_status step_body_captured(hgl_graph* g, StepGraph* sg, const hgl_step_opts& 
   so.flags |= HGL_SOLVE_WARM_START;
   SolveExtras ext;
   ext.fixed_iters = sg->fixed_iters;
+  if (so.dtype != HGL_FP64) HGL_TRY(request_edges(g, c, &ext));
   HGL_TRY(cg_solve_impl(g, w, o.lam, o.lam, sg->Y, sg->ldy, sg->F, sg->ldf, c, P, so, nullptr, nullptr, nullptr, st,
                         true, &ext));
-  if (ext.f32)
-    HGL_TRY(weight_grad_launch(g, w, ext.f32, nullptr, ext.ld32, c, HGL_FP32, o.mu, 0, grad, st));
-  else
-    HGL_TRY(weight_grad_launch(g, w, sg->F, nullptr, sg->ldf, c, HGL_FP64, o.mu, 0, grad, st));
+  HGL_TRY(step_gradient(g, w, ext, sg->F, sg->ldf, c, o.mu, grad, st));
   HGL_CHECK_CUDA(cudaMemcpyAsync(w_old, w, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
   if (o.flags & HGL_STEP_ACTIVE_SET)
     HGL_TRY(active_set_launch(w, grad, o.eta, m, pwork, sms, st));
@@ -313,7 +341,7 @@ hgl_status step_capture(hgl_graph* g, StepGraph* sg, const hgl_step_opts& o) {
     return cuda_error(ei, "cudaGraphInstantiate(adaptive step)", __FILE__, __LINE__);
   }
   sg->deps.clear();
-  for (const Buffer* b : {&g->step, &g->solver, &g->partials, &g->scratch, &g->scratch2, &g->misc})
+  for (const Buffer* b : {&g->step, &g->solver, &g->partials, &g->scratch, &g->scratch2, &g->misc, &g->edge_tf})
     sg->deps.emplace_back(b, b->ptr);
   if (sg->plan) {
     hgl_precond* P = const_cast<hgl_precond*>(precond_plan_handle(sg->plan));

@@ -476,6 +476,52 @@ __global__ void k_as_scale(double* __restrict__ w, const double* __restrict__ v,
 
 }  // namespace
 
+double* grad_vectors(hgl_graph* g, hgl_status* st) {
+  return static_cast<double*>(buffer_get(g->misc, sizeof(double) * (size_t)(g->m + g->n + 2), st));
+}
+
+// The gradient's vertex pass and final sum from a first pass done elsewhere (TF, ex).
+hgl_status weight_grad_from_edges(hgl_graph* g, const double* w, const float* TF, int64_t ldtf, const float* F,
+                                  int64_t ld, int c, double mu, int flags, double* grad, cudaStream_t st) {
+  constexpr int E = 4;
+  const bool frozen = (flags & HGL_GRAD_DV_FROZEN) != 0;
+  const int nvec = (c + E - 1) / E;
+  int lg = 1, nv = 1;
+  pick_tile(std::min(nvec, 128), &lg, &nv);
+  const int cc = lg * nv * E;
+  hgl_status stt = HGL_OK;
+  double* vecs = grad_vectors(g, &stt);
+  if (!vecs) return stt;
+  double* ex = vecs;
+  double* phi = vecs + g->m;
+  const int64_t cap = (int64_t)g->num_sms * 8;
+  const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + OP_WARPS - 1) / OP_WARPS, cap));
+  ProfScope prof(HGL_PROF_GRADIENT, st);
+  if (!frozen) {
+    for (int c0 = 0; c0 < c; c0 += cc) {
+      const int cw = std::min(cc, c - c0);
+#define HGL_GV(LG_, NV_)                                                                                        \
+  else if (lg == LG_ && nv == NV_) {                                                                            \
+    auto fn = k_grad_vertex<float, LG_, NV_, false>;                                                            \
+    const int gr = vertex_grid(g, resident_blocks(reinterpret_cast<const void*>(fn), OP_THREADS, 0));           \
+    hgl::count_launch();                                                                                        \
+    fn<<<gr, OP_THREADS, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, g->s, TF + c0, nullptr, ldtf, F, nullptr, ld,    \
+                                  c0, cw, phi);                                                                 \
+  }
+      if (false) {
+      }
+      HGL_FOR_EACH_TILE(HGL_GV)
+#undef HGL_GV
+      HGL_CHECK_CUDA(cudaGetLastError());
+    }
+  }
+  hgl::count_launch();
+  k_grad_final<<<grid1, OP_THREADS, 0, st>>>(g->m, g->csc_ptr, g->csc_idx, g->de, ex, frozen ? nullptr : phi, w, mu,
+                                             1.0, grad);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}
+
 hgl_status weight_grad_launch(hgl_graph* g, const double* w, const void* F, const void* Zb, int64_t ld, int c,
                               int dtype, double mu, int flags, double* grad, cudaStream_t st, double theta_sign) {
   const bool frozen = (flags & HGL_GRAD_DV_FROZEN) != 0;
