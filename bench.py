@@ -47,7 +47,7 @@ SEED = 20190822
 # the full workload at a given column chunk, from one ncu capture of this bench
 # (profiles/operator_apply_full_adaptive.md, profiles/pair_residual_full_adaptive.md);
 # reported as roofline.traffic only for a run of that workload with that chunk.
-NCU_TRAFFIC_PER_LAUNCH = {("operator", 128): 66.0e9, ("residual", 128): 149.2e9}
+NCU_TRAFFIC_PER_LAUNCH = {("operator", "fp32", 128): 66.0e9, ("residual", "fp32", 128): 149.2e9}
 LOOP = 20           # outer iterations of one adaptive loop
 K_RANK, P_OVER, Q_ITERS = 64, 10, 2
 BCG_S, BCG_STEPS = 32, 4   # block CG comparator: columns per group, outer iterations timed
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--eta", type=float, default=None, help="override the workload's step size")
     ap.add_argument("--no-tune", action="store_true", help="keep the default column chunks (no autotuning)")
     ap.add_argument("--no-graph", action="store_true", help="run each outer iteration eagerly (no CUDA graph)")
+    ap.add_argument("--panels", default="bf16", choices=["fp32", "bf16"],
+                    help="search-direction storage of the headline loop's inner CG (the other is timed beside it)")
     ap.add_argument("--schur", default=None,
                     help="time the nested Schur-complement inverse at these vertex counts (comma list) and exit")
     return ap.parse_args()
@@ -161,10 +163,11 @@ def make_inputs(scale: float):
 
 # ---- algorithmic bytes per launch of each kernel family (index + panels + vectors) ----
 
-def bytes_operator(n, m, nnz, c, elt, chunks=1):
+def bytes_operator(n, m, nnz, c, elt, chunks=1, elt_z=None):
     """Operator apply Z = a X + b Theta X: per column chunk the indices; X read by both
-    passes, the m x c intermediate written and read once, Z written once."""
-    return chunks * (2 * 4 * nnz + 8 * (n + m + 2)) + 2 * n * c * elt + 2 * m * c * 4 + n * c * elt \
+    passes, the m x c intermediate (FP32) written and read once, Z written once."""
+    elt_z = elt if elt_z is None else elt_z
+    return chunks * (2 * 4 * nnz + 8 * (n + m + 2)) + 2 * n * c * elt + 2 * m * c * 4 + n * c * elt_z \
         + 8 * (2 * n + m)
 
 
@@ -299,13 +302,14 @@ def synth_blocks(d):
     return np.asarray(d["block_ptr"], dtype=np.int64)
 
 
-def config_dict(d, bp):
+def config_dict(d, bp, panels="bf16"):
     wl = d["wl"]
     return {"workload": WORKLOAD, "n": d["n"], "m": d["m"], "nnz": int(d["edge_ptr"][-1]), "c": d["c"],
             "lam": wl.lam, "mu": wl.mu, "eta": d.get("eta", wl.eta), "outer_loop": LOOP, "tol_relres": TOL,
             "size_law": synth.describe_sizes(wl), "route": "block rSVD preconditioned CG (BR)",
             "blocks": int(len(bp) - 1), "block_sizes": "U{1024..8192}", "k": K_RANK, "p": P_OVER, "q": Q_ITERS,
-            "panel_dtype": "fp32 (fp64-accurate refinement)",
+            "panel_dtype": ("bf16 search directions, fp32 products, residual and iterate" if panels == "bf16"
+                            else "fp32") + " (fp64-accurate refinement)",
             "block_products": "auto by block fill: fp32 from the incidence lists, or bf16 dense blocks on tcgen05",
             "precond_apply": "tcgen05 tf32, operands split hi+lo (3 products), fp32 accumulate",
             "l2_flush": "inputs larger than L2 (>= 2 GB panels)"}
@@ -387,11 +391,13 @@ def main():
         # pick the column chunks of the gather passes on this graph (untimed setup)
         t0 = time.time()
         op32, pair32, grid32 = hgl.tune_operator(g, w0, c, hgl.HGL_FP32)
+        op16, _, grid16 = hgl.tune_operator(g, w0, c, hgl.HGL_BF16)
         op64, _, grid64 = hgl.tune_operator(g, w0, c, hgl.HGL_FP64)
         policy = ("one wave", "eight per SM")
         broute, b_dense, b_sparse = hgl.tune_block_rsvd(g, w0, bp, K_RANK, P_OVER, Q_ITERS)
-        tuned = {"operator_chunk_fp32": op32, "residual_chunk": pair32, "operator_chunk_fp64": op64,
-                 "grid_fp32": policy[grid32], "grid_fp64": policy[grid64],
+        tuned = {"operator_chunk_fp32": op32, "operator_chunk_bf16": op16, "residual_chunk": pair32,
+                 "operator_chunk_fp64": op64,
+                 "grid_fp32": policy[grid32], "grid_bf16": policy[grid16], "grid_fp64": policy[grid64],
                  "block_products": {"route": "sparse" if broute == hgl.HGL_BLOCKS_SPARSE else "dense (tcgen05)",
                                     "ms_per_build_dense": b_dense, "ms_per_build_sparse": b_sparse},
                  "tune_s": time.time() - t0}
@@ -404,8 +410,12 @@ def main():
     d["eta"] = eta
 
     graph_flag = 0 if args.no_graph else hgl.HGL_STEP_GRAPH
+    # inner-CG search directions of the headline loop (the other type is an arm)
+    head_dt = hgl.HGL_BF16 if args.panels == "bf16" else hgl.HGL_FP32
+    other_dt = hgl.HGL_FP32 if head_dt == hgl.HGL_BF16 else hgl.HGL_BF16
+    pname = {hgl.HGL_FP32: "fp32", hgl.HGL_BF16: "bf16"}
 
-    def step(Fp, wp, i, dtype=hgl.HGL_FP32, route=hgl.HGL_ROUTE_BR, reset=True):
+    def step(Fp, wp, i, dtype=head_dt, route=hgl.HGL_ROUTE_BR, reset=True):
         # one outer iteration; with the graph flag the library replays one captured CUDA
         # graph per call (the first call with these buffers runs eagerly, the second captures)
         if reset and i % LOOP == 0:
@@ -463,17 +473,21 @@ def main():
 
     # roofline of the dominant kernel family (event-timed inside the timed region)
     hbm_peak, bf16_peak, peak_kind = measured_peaks()
-    kernel_names = {hgl.PROF_OPERATOR: "operator apply (k_edge_pass + k_vertex_pass), FP32 panels, c=512",
+    kernel_names = {hgl.PROF_OPERATOR: "operator apply (k_edge_pass + k_vertex_pass), "
+                                        + ("BF16 search directions into FP32 products" if head_dt == hgl.HGL_BF16
+                                           else "FP32 panels") + ", c=512",
                     hgl.PROF_RESIDUAL: "pair-arithmetic residual (df::k_edge + df::k_vertex), c=512",
                     hgl.PROF_OPRESID: "FP32 residual estimate (k_edge_pass + k_vertex_pass, residual epilogue)",
                     hgl.PROF_GEMM: "grouped block GEMM on tcgen05 (umma::k_block_gemm), BF16 in / FP32 out",
                     hgl.PROF_GRADIENT: "weight gradient (k_grad_edge + k_grad_vertex + k_grad_final), FP32"}
     lpad = ((K_RANK + P_OVER + 15) // 16) * 16
-    op_chunk = (tuned or {}).get("operator_chunk_fp32") or 128
+    op_chunk = (tuned or {}).get("operator_chunk_" + pname[head_dt]) or 128
+    op32_chunk = (tuned or {}).get("operator_chunk_fp32") or 128
     pair_chunk = (tuned or {}).get("residual_chunk") or 128
-    per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, 4, -(-c // op_chunk)),
+    elt_x = 2 if head_dt == hgl.HGL_BF16 else 4
+    per_launch_bytes = {hgl.PROF_OPERATOR: bytes_operator(n, m, nnz, c, elt_x, -(-c // op_chunk), elt_z=4),
                         hgl.PROF_RESIDUAL: bytes_residual(n, m, nnz, c, -(-c // pair_chunk)),
-                        hgl.PROF_OPRESID: bytes_opresid(n, m, nnz, c, -(-c // op_chunk)),
+                        hgl.PROF_OPRESID: bytes_opresid(n, m, nnz, c, -(-c // op32_chunk)),
                         hgl.PROF_GEMM: bytes_gemm(bp, lpad),
                         hgl.PROF_GRADIENT: bytes_gradient(n, m, nnz, c)}
     # executed calls of the solver's families: a captured step launches a fixed sequence
@@ -501,7 +515,8 @@ def main():
     dcnt = min(executed.get(dom, dcnt), dcnt)
     davg = dms / max(dcnt, 1)
     achieved = per_launch_bytes[dom] / (davg / 1000.0) / 1e9
-    fam_key = {hgl.PROF_OPERATOR: ("operator", op_chunk), hgl.PROF_RESIDUAL: ("residual", pair_chunk)}.get(dom)
+    fam_key = {hgl.PROF_OPERATOR: ("operator", pname[head_dt], op_chunk),
+               hgl.PROF_RESIDUAL: ("residual", "fp32", pair_chunk)}.get(dom)
     traffic = NCU_TRAFFIC_PER_LAUNCH.get(fam_key) if (args.scale == 1.0 and fam_key) else None
     roofline = {"kernel": kernel_names[dom], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": traffic,
@@ -564,7 +579,8 @@ def main():
         return {"F_max_col_rel": float(dF.max().item()),
                 "w_rel": float((torch.linalg.norm(wa - wb) / torch.linalg.norm(wb)).item())}
 
-    fp64 = mixed_cg = mixed_bf16 = fp64_bcg = loop_acc = None
+    fp64 = mixed_cg = mixed_other = fp64_bcg = loop_acc = None
+    plabel = {hgl.HGL_FP32: "FP32 panels", hgl.HGL_BF16: "BF16 search directions (FP32 products, residual and iterate)"}
     if not args.no_fp64:
         f64_ms, st64, F64, w64 = timed_loop(hgl.HGL_FP64, hgl.HGL_ROUTE_CG)
         fp64 = {"ms_per_step": f64_ms, "value": 1000.0 / f64_ms, "unit": UNIT,
@@ -572,9 +588,9 @@ def main():
                 "cg_iters_per_step": float(np.mean([s.solve.iters for s in st64])),
                 "relres_max": max(s.solve.relres_max for s in st64),
                 "speedup_of_mixed": f64_ms / ms_per_step}
-        cg_ms, stc, Fc, wc = timed_loop(hgl.HGL_FP32, hgl.HGL_ROUTE_CG)
+        cg_ms, stc, Fc, wc = timed_loop(head_dt, hgl.HGL_ROUTE_CG)
         mixed_cg = {"ms_per_step": cg_ms, "value": 1000.0 / cg_ms, "unit": UNIT,
-                    "route": "CG per column, FP32 panels with FP64-accurate refinement, no preconditioner",
+                    "route": f"CG per column, {plabel[head_dt]} with FP64-accurate refinement, no preconditioner",
                     "cg_iters_per_step": float(np.mean([s.solve.iters for s in stc])),
                     "relres_max": max(s.solve.relres_max for s in stc),
                     "speedup_over_fp64": f64_ms / cg_ms}
@@ -600,14 +616,13 @@ def main():
                     "fp64_cg_iters_same_steps": f64_cg_first,
                     "relres_max": max(s.solve.relres_max for s in stk)}
         del Fk, wk
-        bf_ms, stb, Fb, wb = timed_loop(hgl.HGL_BF16, hgl.HGL_ROUTE_BR)
-        mixed_bf16 = {"ms_per_step": bf_ms, "value": 1000.0 / bf_ms, "unit": UNIT,
-                      "route": "block rSVD preconditioned CG, BF16 panels (FP32 accumulate) with FP64-accurate "
-                               "refinement",
-                      "cg_iters_per_step": float(np.mean([s.solve.iters for s in stb])),
-                      "refinements_per_step": float(np.mean([s.solve.refinements for s in stb])),
-                      "relres_max": max(s.solve.relres_max for s in stb),
-                      "speedup_over_fp64": f64_ms / bf_ms}
+        bf_ms, stb, Fb, wb = timed_loop(other_dt, hgl.HGL_ROUTE_BR)
+        mixed_other = {"ms_per_step": bf_ms, "value": 1000.0 / bf_ms, "unit": UNIT,
+                       "route": f"block rSVD preconditioned CG, {plabel[other_dt]} with FP64-accurate refinement",
+                       "cg_iters_per_step": float(np.mean([s.solve.iters for s in stb])),
+                       "refinements_per_step": float(np.mean([s.solve.refinements for s in stb])),
+                       "relres_max": max(s.solve.relres_max for s in stb),
+                       "speedup_over_fp64": f64_ms / bf_ms}
         if loops_compared:
             # the loop's exact trajectory to within 3e-10 per step: FP64 CG to 1e-10,
             # eager launches, the same 20 outer iterations from w0 (untimed)
@@ -620,7 +635,8 @@ def main():
             torch.cuda.synchronize()
             loop_acc = {"reference": "FP64 CG to relres 1e-10, same 20 outer iterations from w0",
                         "mixed_br": loop_diff(F_loop, w_loop, Ft, wt), "fp64_cg": loop_diff(F64, w64, Ft, wt),
-                        "mixed_cg": loop_diff(Fc, wc, Ft, wt), "mixed_bf16_br": loop_diff(Fb, wb, Ft, wt),
+                        "mixed_cg": loop_diff(Fc, wc, Ft, wt),
+                        f"mixed_{pname[other_dt]}_br": loop_diff(Fb, wb, Ft, wt),
                         "mixed_br_vs_fp64_cg": loop_diff(F_loop, w_loop, F64, w64),
                         "bound_F_from_tol": (1 + wl.lam) / wl.lam * TOL}
             del Ft, wt
@@ -635,8 +651,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": dict(config_dict(d, bp), parallelism="replicas" if world > 1 else "single",
+            "vs_baseline": None, "dtype": ("bf16+f32+f64" if head_dt == hgl.HGL_BF16 else "f32+f64"),
+            "data": "synthetic",
+            "config": dict(config_dict(d, bp, pname[head_dt]), parallelism="replicas" if world > 1 else "single",
                            cuda_graph="one captured graph per outer iteration" if graph_flag else "eager launches"),
             "solve": {"cg_iters_per_step": iters, "relres_max": relres_max,
                       "dw_rel_to_uniform_w": dw_rel},
@@ -649,7 +666,7 @@ def main():
             "e2e": e2e,
             "fp64_cg": fp64,
             "mixed_cg_route": mixed_cg,
-            "mixed_bf16_route": mixed_bf16,
+            f"mixed_{pname[other_dt]}_route": mixed_other,
             "fp64_block_cg": fp64_bcg,
             "loop_accuracy": loop_acc,
             "cpu_baseline": cpu,

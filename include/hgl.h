@@ -236,12 +236,14 @@ typedef struct hgl_precond hgl_precond;
 typedef struct {
   double  tol;         /* per-column target ||lam y_j - M f_j|| <= tol ||lam y_j||       */
   int32_t max_iter;    /* cap on CG iterations (all refinement sweeps together)          */
-  int32_t dtype;       /* HGL_FP64: plain FP64 CG.  HGL_FP32 / HGL_BF16: CG on panels of */
-                       /* that type with FP32 arithmetic, inside FP64 iterative          */
-                       /* refinement (residual recomputed FP64-accurately from F)        */
+  int32_t dtype;       /* HGL_FP64: plain FP64 CG.  HGL_FP32: CG on FP32 panels with     */
+                       /* FP32 arithmetic, inside FP64 iterative refinement (residual    */
+                       /* recomputed FP64-accurately from F).  HGL_BF16: the same with   */
+                       /* the search directions stored in BF16 (the operator's input;    */
+                       /* its product, the residual and the iterate stay FP32)           */
   double  inner_tol;   /* mixed modes: floor of the relative reduction asked of each     */
-                       /* inner solve; a sweep aims at max(inner_tol, 0.1 tol/relres)    */
-                       /* (0 = 1e-5 for FP32, 1e-2 for BF16)                             */
+                       /* inner solve; a sweep aims at max(inner_tol, 0.5 tol/relres)    */
+                       /* (0 = 1e-5)                                                     */
   int32_t max_refine;  /* mixed modes: cap on refinement sweeps (0 = 8)                  */
   int32_t flags;       /* HGL_SOLVE_WARM_START                                           */
 } hgl_solve_opts;

@@ -138,10 +138,11 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
     oZ = precond ? take(sizeof(float) * n * sm->ld32) : 0;
     oX = take(sizeof(float) * n * sm->ld32);
   }
-  size_t oFh = 0, oFl = 0, oSc = 0;
+  size_t oFh = 0, oFl = 0, oFl16 = 0, oSc = 0;
   if (mode != HGL_FP64) {
     oFh = take(sizeof(float) * n * sm->ld32);
     oFl = take(sizeof(float) * n * sm->ld32);
+    oFl16 = take(sizeof(uint16_t) * n * sm->ld16);
     oSc = take(sizeof(float) * 2 * (size_t)(g->n + g->m));
   }
   size_t oVec = take(sizeof(double) * 8 * (size_t)c);
@@ -157,6 +158,7 @@ hgl_status solver_layout(hgl_graph* g, int c, int mode, bool precond, SolverMem*
   if (mode != HGL_FP64) {
     sm->Fh = reinterpret_cast<float*>(base + oFh);
     sm->Fl = reinterpret_cast<float*>(base + oFl);
+    sm->Fl16 = reinterpret_cast<bf16_t*>(base + oFl16);
     sm->s_hi = reinterpret_cast<float*>(base + oSc);
     sm->s_lo = sm->s_hi + g->n;
     sm->t_hi = sm->s_lo + g->n;
@@ -406,22 +408,32 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
     return verdict;
   }
 
-  // mixed precision: FP64 refinement around an FP32-arithmetic CG
-  const double inner_tol = o.inner_tol > 0 ? o.inner_tol : (mode == HGL_BF16 ? 1e-2 : 1e-5);
+  // mixed precision: FP64 refinement around an FP32-arithmetic CG.  With BF16 search
+  // directions the inner CG still reaches FP32 rates: alpha comes from the stored p and
+  // its product M p, and x and r move along that same p, so r stays the residual of x;
+  // rounding p to BF16 (2^-9 relative) only perturbs which direction is taken, and the
+  // loss of conjugacy that causes is far below what the inner tolerance needs.
+  const double inner_tol = o.inner_tol > 0 ? o.inner_tol : 1e-5;
   const int max_refine = o.max_refine > 0 ? o.max_refine : 8;
   float* R32 = static_cast<float*>(sm.R);
   float* X32 = static_cast<float*>(sm.X);
   // the iterate F lives as an FP32 pair (hi, lo) during refinement; the residual is
   // formed from the pair in pair arithmetic (FP64-accurate, no FP64 arithmetic)
+  // Compact residual: the gather passes read F's low part (and store the intermediate's)
+  // in BF16, which adds at most 2^-32 ||F_j|| <= 2^-32 / lam ||gy y_j|| to a column's
+  // residual (||F_j|| <= ||gy y_j|| / lam since M >= lam I); taken when that is below
+  // tol / 64, i.e. where it cannot move a convergence decision.
+  const bool compact = tol >= 64.0 * 0x1p-32 / lam;
+  bf16_t* Fl16 = compact ? sm.Fl16 : nullptr;
   HGL_TRY(df_split_scalings(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, st));
-  HGL_TRY(df_panel_op(g, 0, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st));
+  HGL_TRY(df_panel_op(g, 0, c, F, ldf, sm.Fh, sm.Fl, sm.ld32, nullptr, st, nullptr, Fl16, sm.ld16));
   // FP64-accurate residual from the pair; with a guard, skipped (launches and
   // reduction) when *guard == 0, leaving the previous relres in place
   auto residual = [&](const int32_t* guard) -> hgl_status {
     int rr_rows = 0;
     HGL_TRY(df_residual(g, sm.s_hi, sm.s_lo, sm.t_hi, sm.t_lo, sm.Fh, sm.Fl, sm.ld32, Y, ldy, -(1.0 + lam), 1.0, gy,
                         c, R32, sm.pa, st, &rr_rows, guard, extras ? extras->edge_tf : nullptr,
-                        extras ? extras->edge_ldtf : 0, extras ? extras->edge_ex : nullptr));
+                        extras ? extras->edge_ldtf : 0, extras ? extras->edge_ex : nullptr, Fl16, sm.ld16));
     CgState Sg = S;
     Sg.guard = guard;
     return cg_reduce<RED_RESID>(sm.pa, nullptr, rr_rows, Sg, st);
@@ -432,8 +444,7 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
   // enters the first correction; the solve starts from it when that error is well
   // below tol.  It never ends a solve: every convergence decision and every reported
   // residual comes from the pair residual.
-  const bool cheap_first =
-      mode == HGL_FP32 && tol >= 4.0 * 0x1p-24 * (1.0 + 2.0 * (1.0 + lam) / lam);
+  const bool cheap_first = tol >= 4.0 * 0x1p-24 * (1.0 + 2.0 * (1.0 + lam) / lam);
   auto residual_f32 = [&]() -> hgl_status {
     OpCall cl{};
     cl.g = g;
@@ -518,19 +529,18 @@ hgl_status cg_solve_impl(hgl_graph* g, const double* w, double lam, double gy, c
                                            done)));
       }
     }
-    return df_panel_op(g, 1, c, nullptr, 0, sm.Fh, sm.Fl, sm.ld32, X32, st, guard);
+    return df_panel_op(g, 1, c, nullptr, 0, sm.Fh, sm.Fl, sm.ld32, X32, st, guard, Fl16, sm.ld16);
   };
 
   if (extras && extras->fixed_iters > 0) {
     // capture mode: a fixed launch sequence without host reads -- the residual, then
     // guarded sweeps (the first ones of the eager loop) each followed by a guarded
     // residual; a sweep runs, on the device's decision, only when the previous one fell
-    // short of tol.  One FP32 sweep reaches about 1e-7 times the starting relres and at
-    // most the inner floor, so two suffice; a BF16 sweep gains about 1e-2 (the BF16
-    // rounding of the search directions bounds the inner solve), so BF16 panels get
-    // four.  Statistics stay on the device.
+    // short of tol.  One sweep (FP32 or BF16 search directions) reaches about 1e-7
+    // times the starting relres and at most the inner floor, so two suffice.
+    // Statistics stay on the device.
     const double floor = inner_tol;
-    const int nsweeps = mode == HGL_BF16 ? 4 : 2;
+    const int nsweeps = 2;
     int done = 0;
     HGL_TRY(cheap_first ? residual_f32() : residual(nullptr));
     for (int sw = 0; sw < nsweeps; ++sw) {

@@ -65,16 +65,19 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
 
 constexpr int THREADS = 256;
 
-// hyperedge pass: T[e] = t_e sum_{v in e} s_v F[v]     (F, T as hi/lo FP32 panels)
+// hyperedge pass: T[e] = t_e sum_{v in e} s_v F[v]     (F, T as hi/lo panels)
 // Heavy hyperedges (the first nheavy of `order`) get one block each; light ones one
 // warp each, longest first (as in the operator's hyperedge pass).
-template <int LG, int NV>
+// LO is the storage of the low parts that the passes gather (F's and T's): float, or
+// bf16_t for the compact residual (the low parts rounded to BF16 cost at most 2^-9 of
+// a low part, i.e. 2^-33 of the high part, instead of ~2^-48).
+template <int LG, int NV, class LO>
 __global__ void __launch_bounds__(THREADS)
 k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
        const int32_t* __restrict__ order, int64_t nheavy, const float* __restrict__ s_hi,
        const float* __restrict__ s_lo, const float* __restrict__ t_hi, const float* __restrict__ t_lo,
-       const float* __restrict__ Fh, const float* __restrict__ Fl, int64_t ldf, int c0, int cw,
-       float* __restrict__ Th, float* __restrict__ Tl, int64_t ldt, const int32_t* __restrict__ guard,
+       const float* __restrict__ Fh, int64_t ldf, const LO* __restrict__ Fl, int64_t ldfl, int c0, int cw,
+       float* __restrict__ Th, LO* __restrict__ Tl, int64_t ldt, const int32_t* __restrict__ guard,
        float* __restrict__ tf, int64_t ldtf, double* __restrict__ ex) {
   if (guard && *guard == 0) return;
   constexpr int E = 4, G = 32 / LG, WARPS = THREADS / 32, TILE = LG * NV * E;
@@ -101,7 +104,7 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
         if (col < cw) {
           float xh[E], xl[E];
           vload<float, float, E>(Fh + (int64_t)v * ldf + c0 + col, xh);
-          vload<float, float, E>(Fl + (int64_t)v * ldf + c0 + col, xl);
+          vload<float, LO, E>(Fl + (int64_t)v * ldfl + c0 + col, xl);
 #pragma unroll
           for (int j = 0; j < E; ++j) fma2(acc[k][j], sv, f2{xh[j], xl[j]});
         }
@@ -154,7 +157,7 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
             d += (double)acc[k][j].hi * (double)acc[k][j].hi;
           }
           vstore<float, float, E>(Th + e * ldt + col, oh, E);
-          vstore<float, float, E>(Tl + e * ldt + col, ol, E);
+          vstore<LO, float, E>(Tl + e * ldt + col, ol, E);
           // the gradient's t * sigma in FP32, full width, at the residual's (final) F
           if (tf) vstore<float, float, E>(tf + e * ldtf + c0 + col, oh, E);
         }
@@ -171,11 +174,11 @@ k_edge(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict
 
 // vertex pass: z = gy Y[v] + a F[v] + b s_v sum_{e ni v} T[e];  R = fl32(z);
 // partials of R.R per column (compensated FP32, FP64 across rows).
-template <int LG, int NV>
+template <int LG, int NV, class LO>
 __global__ void __launch_bounds__(THREADS)
 k_vertex(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
          const float* __restrict__ s_hi, const float* __restrict__ s_lo, const float* __restrict__ Th,
-         const float* __restrict__ Tl, int64_t ldt, const float* __restrict__ Fh, const float* __restrict__ Fl,
+         const LO* __restrict__ Tl, int64_t ldt, const float* __restrict__ Fh, const float* __restrict__ Fl,
          int64_t ldf, const double* __restrict__ Y, int64_t ldy, double a, double b, double gy, int c0, int cw, int c,
          float* __restrict__ R, int64_t ldr, double* __restrict__ partials, const int32_t* __restrict__ guard) {
   if (guard && *guard == 0) return;
@@ -200,7 +203,7 @@ k_vertex(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restri
         if (col < cw) {
           float xh[E], xl[E];
           vload<float, float, E>(Th + (int64_t)e * ldt + col, xh);
-          vload<float, float, E>(Tl + (int64_t)e * ldt + col, xl);
+          vload<float, LO, E>(Tl + (int64_t)e * ldt + col, xl);
 #pragma unroll
           for (int j = 0; j < E; ++j) add2(acc[k][j], f2{xh[j], xl[j]});
         }
@@ -265,13 +268,14 @@ __global__ void k_split_vec(int64_t len, const double* __restrict__ x, float* __
 }
 
 // (Fh, Fl) <- F (FP64 panel), or (Fh, Fl) += D (FP32 panel), or F <- Fh + Fl.
-// One thread per 4-column vector of a row.
+// With Fl16, SPLIT and ACCUMULATE also store the low part rounded to BF16 (the copy the
+// compact residual gathers).  One thread per 4-column vector of a row.
 enum PanelOp : int { SPLIT = 0, ACCUMULATE = 1, COMBINE = 2 };
 
 template <int OP>
 __global__ void k_panel(int64_t n, int c, double* __restrict__ F, int64_t ldf, float* __restrict__ Fh,
                         float* __restrict__ Fl, int64_t ld32, const float* __restrict__ D,
-                        const int32_t* __restrict__ guard) {
+                        const int32_t* __restrict__ guard, bf16_t* __restrict__ Fl16, int64_t ld16) {
   if (guard && *guard == 0) return;
   const int vecs = (c + 3) / 4;
   const int64_t total = n * vecs;
@@ -289,6 +293,7 @@ __global__ void k_panel(int64_t n, int c, double* __restrict__ F, int64_t ldf, f
       }
       vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
       vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
+      if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
     } else if (OP == ACCUMULATE) {
       float d[4];
       vload<float, float, 4, false>(Fh + r * ld32 + col, h);
@@ -304,6 +309,7 @@ __global__ void k_panel(int64_t n, int c, double* __restrict__ F, int64_t ldf, f
       }
       vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
       vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
+      if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
     } else {
       vload<float, float, 4, false>(Fh + r * ld32 + col, h);
       vload<float, float, 4, false>(Fl + r * ld32 + col, lo);

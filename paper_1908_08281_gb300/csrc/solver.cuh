@@ -28,6 +28,7 @@ struct SolverMem {
   void* int_base = nullptr;  // per-column int32 state and flags (zeroed per solve)
   size_t int_bytes = 0;
   float *Fh = nullptr, *Fl = nullptr;          // mixed modes: F as an FP32 pair
+  bf16_t* Fl16 = nullptr;                      // mixed modes: F's low part in BF16 (compact residual)
   float *s_hi = nullptr, *s_lo = nullptr;      // mixed modes: scalings as FP32 pairs
   float *t_hi = nullptr, *t_lo = nullptr;
 };
@@ -60,13 +61,16 @@ hgl_status fill_stats(const CgState& S, int c, int refinements, double tol, doub
 
 hgl_status df_split_scalings(const hgl_graph* g, float* s_hi, float* s_lo, float* t_hi, float* t_lo, cudaStream_t st);
 // guard (optional device flag): the kernels return at once when *guard == 0
+// Fl16 (optional): SPLIT and ACCUMULATE also store the low part rounded to BF16
 hgl_status df_panel_op(const hgl_graph* g, int op, int c, double* F, int64_t ldf, float* Fh, float* Fl, int64_t ld32,
-                       const float* D, cudaStream_t st, const int32_t* guard = nullptr);
+                       const float* D, cudaStream_t st, const int32_t* guard = nullptr, bf16_t* Fl16 = nullptr,
+                       int64_t ld16 = 0);
+// Fl16 (optional): the compact residual, gathering F's low part from its BF16 copy
 hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const float* t_hi, const float* t_lo,
                        const float* Fh, const float* Fl, int64_t ld32, const double* Y, int64_t ldy, double a,
                        double b, double gy, int c, float* R, double* partials, cudaStream_t st, int* rows,
                        const int32_t* guard = nullptr, float* tf = nullptr, int64_t ldtf = 0,
-                       double* ex = nullptr);
+                       double* ex = nullptr, const bf16_t* Fl16 = nullptr, int64_t ld16 = 0);
 
 hgl_status cg_reduce_beta(double* pa, int rows_a, double* pb, int rows_b, const CgState& S, cudaStream_t st);
 

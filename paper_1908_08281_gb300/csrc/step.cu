@@ -427,7 +427,7 @@ hgl_status adaptive_step_impl(hgl_graph* g, double* w, const hgl_step_opts& o, c
     ng->route = o.route;
     ng->flags = o.flags;
     ng->solve = o.solve;
-    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : (o.solve.dtype == HGL_BF16 ? 1e-2 : 1e-5);
+    const double floor = o.solve.inner_tol > 0 ? o.solve.inner_tol : 1e-5;
     ng->fixed_iters = cg_iteration_bound(o.lam, o.solve.dtype == HGL_FP64 ? (o.solve.tol > 0 ? o.solve.tol : 1e-10)
                                                                            : floor) + 4;
     hgl_status e = HGL_OK;

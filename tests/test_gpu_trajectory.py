@@ -42,13 +42,15 @@ def loop():
     return wl, d, H, g, eta, trace
 
 
+@pytest.mark.parametrize("dtype", [hgl.HGL_FP32, hgl.HGL_BF16])
 @pytest.mark.parametrize("route", [hgl.HGL_ROUTE_BR, hgl.HGL_ROUTE_CG])
 @pytest.mark.parametrize("flags", [0, hgl.HGL_STEP_GRAPH])
-def test_mixed_trajectory_matches_oracle_loop(loop, route, flags):
-    """FP32 panels with FP64-accurate refinement, eager and captured (the first call
-    eager, the second captured, later ones replayed), block-rSVD preconditioned or
-    plain CG: after every outer iteration F (the solve at the step's w) and the new w
-    agree with the oracle's loop (FP64 CG to 1e-12) to 1e-5 relative."""
+def test_mixed_trajectory_matches_oracle_loop(loop, route, flags, dtype):
+    """FP32 panels (or BF16 search directions) with FP64-accurate refinement, eager and
+    captured (the first call eager, the second captured, later ones replayed),
+    block-rSVD preconditioned or plain CG: after every outer iteration F (the solve at
+    the step's w) and the new w agree with the oracle's loop (FP64 CG to 1e-12) to 1e-5
+    relative."""
     wl, d, H, g, eta, trace = loop
     Y = hgl.padded_panel(d["n"], d["c"], torch.float64, DEV)
     Y.copy_(torch.from_numpy(d["Y"]))
@@ -58,7 +60,7 @@ def test_mixed_trajectory_matches_oracle_loop(loop, route, flags):
     moved = []
     for i in range(STEPS):
         w_before = w.clone()
-        st = hgl.adaptive_step(g, w, Y, F, lam=wl.lam, mu=wl.mu, eta=eta, tol=TOL, dtype=hgl.HGL_FP32, route=route,
+        st = hgl.adaptive_step(g, w, Y, F, lam=wl.lam, mu=wl.mu, eta=eta, tol=TOL, dtype=dtype, route=route,
                                block_ptr=d["block_ptr"], k=16, p=8, q=2, seed=SEED + i, flags=flags)
         assert st.solve.relres_max <= TOL, (i, st.solve.relres_max)
         Fo, wo = trace[i]["F"], trace[i]["w_new"]
