@@ -206,10 +206,41 @@ __global__ void k_degrees(int64_t n, int64_t m, const int64_t* __restrict__ csr_
   }
 }
 
+// The operator's small-hyperedge terms at the current scalings: per entry (v, e) of a
+// vertex u the coefficient t_e s_v, per vertex s_u^2 times the sum of t_e over its small
+// hyperedges (hyperedge order).
+__global__ void k_small_coef(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+                             const int32_t* __restrict__ de, const int64_t* __restrict__ sptr,
+                             const int32_t* __restrict__ sv, const int32_t* __restrict__ se,
+                             const double* __restrict__ s, const double* __restrict__ t,
+                             double* __restrict__ coef, float* __restrict__ coef32, double* __restrict__ diag,
+                             float* __restrict__ diag32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += stride) {
+    double d = 0.0;
+    for (int64_t i = csr_ptr[u], end = csr_ptr[u + 1]; i < end; ++i) {
+      const int32_t e = csr_idx[i];
+      if (de[e] <= SMALL_EDGE) d += t[e];
+    }
+    const double su = s[u];
+    diag[u] = su * su * d;
+    diag32[u] = (float)(su * su * d);
+    for (int64_t k = sptr[u], end = sptr[u + 1]; k < end; ++k) {
+      const double cf = t[se[k]] * s[sv[k]];
+      coef[k] = cf;
+      coef32[k] = (float)cf;
+    }
+  }
+}
+
 hgl_status degrees_launch(const hgl_graph* g, const double* w, cudaStream_t st) {
   int blocks = g->num_sms * 8;
   hgl::count_launch(); k_degrees<<<blocks, 256, 0, st>>>(g->n, g->m, g->csr_ptr, g->csr_idx, g->de, w, g->dv, g->s, g->t,
                                                          g->s32, g->t32);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  hgl::count_launch();
+  k_small_coef<<<blocks, 256, 0, st>>>(g->n, g->csr_ptr, g->csr_idx, g->de, g->scsr_ptr, g->scsr_v, g->scsr_e, g->s,
+                                       g->t, g->scoef, g->scoef32, g->sdiag, g->sdiag32);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }
@@ -278,6 +309,15 @@ void hgl_graph_destroy(hgl_graph* g) {
   cudaFree(g->s32);
   cudaFree(g->t32);
   cudaFree(g->edge_order);
+  cudaFree(g->lcsr_ptr);
+  cudaFree(g->lcsr_idx);
+  cudaFree(g->scsr_ptr);
+  cudaFree(g->scsr_v);
+  cudaFree(g->scsr_e);
+  cudaFree(g->scoef);
+  cudaFree(g->scoef32);
+  cudaFree(g->sdiag);
+  cudaFree(g->sdiag32);
   hgl::buffer_free(g->scratch);
   hgl::buffer_free(g->scratch2);
   hgl::buffer_free(g->partials);

@@ -280,6 +280,54 @@ hgl_status bits_status(unsigned b) {
   return HGL_OK;
 }
 
+// Split of the operator (see hgl_graph): per vertex, the number of its large hyperedges
+// and of its entries over small ones (members other than itself).
+__global__ void k_split_count(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+                              const int32_t* __restrict__ de, unsigned* __restrict__ lcnt,
+                              unsigned* __restrict__ scnt) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    unsigned a = 0, b = 0;
+    for (int64_t i = csr_ptr[v], end = csr_ptr[v + 1]; i < end; ++i) {
+      const int d = de[csr_idx[i]];
+      if (d > SMALL_EDGE) ++a; else b += (unsigned)(d - 1);
+    }
+    lcnt[v] = a;
+    scnt[v] = b;
+  }
+}
+
+__global__ void k_edge_slots(int64_t m_large, const int32_t* __restrict__ order, int32_t* __restrict__ slot) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m_large; q += (int64_t)gridDim.x * blockDim.x)
+    slot[order[q]] = (int32_t)q;
+}
+
+// Per vertex, in its hyperedge order: the slots of the large hyperedges, and for each
+// small hyperedge its other members (member order) with the hyperedge.
+__global__ void k_split_fill(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+                             const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
+                             const int32_t* __restrict__ de, const int32_t* __restrict__ slot,
+                             const int64_t* __restrict__ lptr, int32_t* __restrict__ lidx,
+                             const int64_t* __restrict__ sptr, int32_t* __restrict__ sv, int32_t* __restrict__ se) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lp = lptr[v], sp = sptr[v];
+    for (int64_t i = csr_ptr[v], end = csr_ptr[v + 1]; i < end; ++i) {
+      const int32_t e = csr_idx[i];
+      if (de[e] > SMALL_EDGE) {
+        lidx[lp++] = slot[e];
+      } else {
+        for (int64_t j = csc_ptr[e]; j < csc_ptr[e + 1]; ++j) {
+          const int32_t u = csc_idx[j];
+          if (u != v) {
+            sv[sp] = u;
+            se[sp] = e;
+            ++sp;
+          }
+        }
+      }
+    }
+  }
+}
+
 // Hyperedges in decreasing size order (stable counting sort on the host; one-time).
 // The gather passes give each hyperedge above HEAVY_ROW members a whole thread block
 // and schedule the rest longest first, so no long row finishes last.
@@ -300,10 +348,12 @@ hgl_status order_edges(hgl_graph* g, cudaStream_t st) {
   }
   std::vector<int32_t> order(m);
   g->nheavy = 0;
+  g->m_large = 0;
   for (int64_t e = 0; e < m; ++e) {
     const int64_t sz = ptr[e + 1] - ptr[e];
     order[count[maxs - sz]++] = (int32_t)e;
     if (sz > HEAVY_ROW) g->nheavy++;
+    if (sz > SMALL_EDGE) g->m_large++;
   }
   HGL_CHECK_CUDA(cudaMalloc(&g->edge_order, sizeof(int32_t) * m));
   HGL_CHECK_CUDA(cudaMemcpyAsync(g->edge_order, order.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
@@ -381,6 +431,35 @@ hgl_status build(int64_t n, int64_t m, const int64_t* edge_ptr, const int32_t* m
   HGL_CHECK_CUDA(cudaGetLastError());
   HGL_TRY(segmented_sort(g->csr_ptr, g->csr_idx, n, list_a, list_b, counts, sms, st));
   HGL_TRY(order_edges(g, st));
+
+  // the operator's split into large hyperedges (through the intermediate, by slot) and
+  // small ones (vertex-to-vertex entries); cnt and cursor are free again, list_a holds
+  // the slots
+  HGL_CHECK_CUDA(cudaMalloc(&g->lcsr_ptr, sizeof(int64_t) * (n + 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->scsr_ptr, sizeof(int64_t) * (n + 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->sdiag, sizeof(double) * n));
+  HGL_CHECK_CUDA(cudaMalloc(&g->sdiag32, sizeof(float) * n));
+  hgl::count_launch(); k_split_count<<<sms * 8, 256, 0, st>>>(n, g->csr_ptr, g->csr_idx, g->de, cnt, cursor);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  HGL_TRY(exclusive_scan(cnt, n, g->lcsr_ptr, tile_sums, st));
+  HGL_TRY(exclusive_scan(cursor, n, g->scsr_ptr, tile_sums, st));
+  int64_t nl = 0, ns = 0;
+  HGL_CHECK_CUDA(cudaMemcpyAsync(&nl, g->lcsr_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaMemcpyAsync(&ns, g->scsr_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  HGL_CHECK_CUDA(cudaMalloc(&g->lcsr_idx, sizeof(int32_t) * (size_t)(nl > 0 ? nl : 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->scsr_v, sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->scsr_e, sizeof(int32_t) * (size_t)(ns > 0 ? ns : 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->scoef, sizeof(double) * (size_t)(ns > 0 ? ns : 1)));
+  HGL_CHECK_CUDA(cudaMalloc(&g->scoef32, sizeof(float) * (size_t)(ns > 0 ? ns : 1)));
+  if (g->m_large > 0) {
+    hgl::count_launch(); k_edge_slots<<<sms * 8, 256, 0, st>>>(g->m_large, g->edge_order, list_a);
+    HGL_CHECK_CUDA(cudaGetLastError());
+  }
+  hgl::count_launch();
+  k_split_fill<<<sms * 8, 256, 0, st>>>(n, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->de, list_a, g->lcsr_ptr,
+                                        g->lcsr_idx, g->scsr_ptr, g->scsr_v, g->scsr_e);
+  HGL_CHECK_CUDA(cudaGetLastError());
   HGL_CHECK_CUDA(cudaStreamSynchronize(st));
   return HGL_OK;
 }

@@ -35,6 +35,8 @@ int device_sm_count();
 int resident_blocks(const void* fn, int threads, size_t smem);
 
 constexpr int TUNE_PAIR = 7;
+// tune_key(TUNE_PAIR16, c) -> chunk of the compact pair residual (BF16 low parts)
+constexpr int TUNE_PAIR16 = 8;
 // tune_key(TUNE_GRID + panel kind, c) -> grid policy of the operator's gather passes:
 // 1 = eight blocks per SM (several waves), otherwise the blocks resident at once
 constexpr int TUNE_GRID = 16;
@@ -44,6 +46,10 @@ inline int tuned_chunk_vecs(const hgl_graph* g, int kind, int c);
 
 // Rows (hyperedges) longer than this go to a whole thread block in the gather passes.
 constexpr int64_t HEAVY_ROW = 128;
+// Hyperedges of at most this many members skip the operator's intermediate: the vertex
+// pass reads their other members' rows directly.  Per hyperedge of size d that costs
+// d (d - 1) row reads instead of d reads, one intermediate row written and d read.
+constexpr int SMALL_EDGE = 3;
 
 // Process-wide count of kernels launched by the library (diagnostics).
 void count_launch(unsigned n = 1);
@@ -114,6 +120,20 @@ struct hgl_graph {
   // processed by a whole thread block each, the rest by one warp each in this order
   int32_t* edge_order = nullptr;  // m
   int64_t nheavy = 0;
+  // Split of Theta for the operator: hyperedges with more than SMALL_EDGE members (the
+  // first m_large of edge_order) go through the m_large x chunk intermediate, indexed
+  // by their position in edge_order (their slot); smaller ones enter the vertex pass
+  // directly as vertex-to-vertex terms t_e s_v X[v] (and a diagonal term).
+  int64_t m_large = 0;
+  int64_t* lcsr_ptr = nullptr;  // n+1
+  int32_t* lcsr_idx = nullptr;  // slots of each vertex's large hyperedges, hyperedge order
+  int64_t* scsr_ptr = nullptr;  // n+1
+  int32_t* scsr_v = nullptr;    // per vertex, over its small hyperedges: the other members
+  int32_t* scsr_e = nullptr;    //   and the hyperedge they share
+  double* scoef = nullptr;      // t_e s_v per small entry (for the w of the last degrees call)
+  float* scoef32 = nullptr;
+  double* sdiag = nullptr;      // n: s_v^2 sum of t_e over the small hyperedges of v
+  float* sdiag32 = nullptr;
   // column chunk (in 16-byte vectors per row) chosen by hgl_tune_operator, keyed by
   // (panel kind, c); kind = HGL_FP64/FP32/BF16 for the operator, TUNE_PAIR for the
   // pair-arithmetic residual
@@ -199,6 +219,12 @@ namespace hgl {
 template <class A> inline const A* scal_s(const hgl_graph* g);
 template <> inline const double* scal_s<double>(const hgl_graph* g) { return g->s; }
 template <> inline const float* scal_s<float>(const hgl_graph* g) { return g->s32; }
+template <class A> inline const A* scal_coef(const hgl_graph* g);
+template <> inline const double* scal_coef<double>(const hgl_graph* g) { return g->scoef; }
+template <> inline const float* scal_coef<float>(const hgl_graph* g) { return g->scoef32; }
+template <class A> inline const A* scal_diag(const hgl_graph* g);
+template <> inline const double* scal_diag<double>(const hgl_graph* g) { return g->sdiag; }
+template <> inline const float* scal_diag<float>(const hgl_graph* g) { return g->sdiag32; }
 template <class A> inline const A* scal_t(const hgl_graph* g);
 template <> inline const double* scal_t<double>(const hgl_graph* g) { return g->t; }
 template <> inline const float* scal_t<float>(const hgl_graph* g) { return g->t32; }

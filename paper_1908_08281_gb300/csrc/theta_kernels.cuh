@@ -1,9 +1,14 @@
 // theta_kernels.cuh -- the two gather passes that apply Theta (Eq. 1) matrix-free.
 //
-//   hyperedge pass:  T[e, :] = t_e * sum_{v in e} s_v X[v, :]           (W De^-1 H^T Dv^-1/2 X)
-//   vertex pass:     Z[v, :] = a X[v, :] + b s_v sum_{e ni v} T[e, :]   (+ gy Y[v, :])
+//   hyperedge pass:  T[q, :] = t_e * sum_{v in e} s_v X[v, :]  for the large hyperedges
+//                    e = order[q] (more than SMALL_EDGE members)   (W De^-1 H^T Dv^-1/2 X)
+//   vertex pass:     Z[u, :] = a X[u, :] + b s_u (sum_{large e ni u} T[slot(e), :]
+//                              + sum_{small e ni u} t_e sum_{v in e} s_v X[v, :])   (+ gy Y[u, :])
 //
-// with s = dv^-1/2 and t = w / de.  Both passes are row gathers over the compressed
+// with s = dv^-1/2 and t = w / de.  A small hyperedge's terms are read straight from X
+// by its members (the v = u term is the per-vertex diagonal s_u^2 sum t_e), which for
+// d <= SMALL_EDGE members moves fewer bytes than an intermediate row written once and
+// gathered d times.  Both passes are row gathers over the compressed
 // layouts: one warp owns one output row at a time; the warp is split into G = 32/LG
 // groups of LG lanes, each group reads one input row per step (16-byte vector loads,
 // NV vectors per lane), and the groups are summed with a shuffle butterfly.  The
@@ -18,6 +23,15 @@ namespace hgl {
 
 constexpr int OP_THREADS = 256;
 constexpr int OP_WARPS = OP_THREADS / 32;
+
+// The small hyperedges' terms of the vertex pass (hgl_graph::scsr_*, scoef, sdiag).
+template <class A>
+struct SmallTerms {
+  const int64_t* ptr;  // n+1
+  const int32_t* nb;   // other member of a small hyperedge
+  const A* coef;       // t_e s_nb
+  const A* diag;       // n: s_u^2 sum_{small e ni u} t_e
+};
 
 // z + gy y of the residual epilogue: in FP64 for FP64 accumulators, in FP32 for FP32
 // ones (an FP32 residual is an estimate: its rounding, a few units of 2^-24 of |lam Y|,
@@ -93,12 +107,13 @@ __device__ __forceinline__ void edge_heavy_block(const int64_t* __restrict__ csc
           for (int w = 0; w < OP_WARPS; ++w) sum += red[w][col + j];
           o[j] = te * sum;
         }
-        vstore<TT, A, E>(Tp + (int64_t)e * ldt + col, o, E);
+        vstore<TT, A, E>(Tp + (int64_t)blockIdx.x * ldt + col, o, E);
       }
     }
   }
 }
 
+// m: the number of large hyperedges (slots 0 .. m-1 of `order`); T row q is slot q.
 template <class TX, class TT, int LG, int NV>
 __global__ void __launch_bounds__(OP_THREADS)
 k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __restrict__ csc_idx,
@@ -176,7 +191,7 @@ k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
           A o[E];
 #pragma unroll
           for (int j = 0; j < E; ++j) o[j] = te * acc[k][j];
-          vstore<TT, A, E>(Tp + (int64_t)e * ldt + col, o, E);
+          vstore<TT, A, E>(Tp + q * ldt + col, o, E);
         }
       }
     }
@@ -186,6 +201,7 @@ k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
 template <class TX, class TT, class TZ, int LG, int NV, int EPI>
 __global__ void __launch_bounds__(OP_THREADS)
 k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+              const SmallTerms<typename AccOf<TX>::type> sm,
               const typename AccOf<TX>::type* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
               int64_t ldx, TZ* __restrict__ Z, int64_t ldz, int c0, int cw, int c, double a, double b,
               const double* __restrict__ Y, int64_t ldy, double gy, double* __restrict__ partials,
@@ -240,6 +256,21 @@ k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
         }
       }
     }
+    // small hyperedges: the other members' rows of X, weighted by t_e s_nb
+    for (int64_t k2 = __ldg(sm.ptr + v) + grp, kend = __ldg(sm.ptr + v + 1); k2 < kend; k2 += G) {
+      const int32_t u = __ldg(sm.nb + k2);
+      const A cf = __ldg(sm.coef + k2);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int col = (k * LG + l) * E;
+        if (col < cw) {
+          A x[E];
+          vload<A, TX, E>(X + (int64_t)u * ldx + c0 + col, x);
+#pragma unroll
+          for (int j = 0; j < E; ++j) acc[k][j] = fma(cf, x[j], acc[k][j]);
+        }
+      }
+    }
 #pragma unroll
     for (int off = LG; off < 32; off <<= 1)
 #pragma unroll
@@ -248,6 +279,7 @@ k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
         for (int j = 0; j < E; ++j) acc[k][j] += __shfl_xor_sync(0xffffffffu, acc[k][j], off);
     if (grp == 0) {
       const A sb = bb * (A)__ldg(s + v);
+      const A ad = aa + bb * __ldg(sm.diag + v);
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
         const int col = (k * LG + l) * E;
@@ -255,7 +287,7 @@ k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
           A x[E], z[E];
           vload<A, TX, E>(X + v * ldx + c0 + col, x);
 #pragma unroll
-          for (int j = 0; j < E; ++j) z[j] = fma(aa, x[j], sb * acc[k][j]);
+          for (int j = 0; j < E; ++j) z[j] = fma(ad, x[j], sb * acc[k][j]);
           if constexpr (EPI == EPI_RESID) {
             double y[E];
             const int nv = cw - col < E ? cw - col : E;
@@ -364,7 +396,7 @@ k_edge_rows(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
       A o[E];
 #pragma unroll
       for (int j = 0; j < E; ++j) o[j] = te * acc[j];
-      vstore<TT, A, E>(Tp + (int64_t)e * ldt + col, o, E);
+      vstore<TT, A, E>(Tp + q * ldt + col, o, E);
     }
   }
 }
@@ -372,6 +404,7 @@ k_edge_rows(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
 template <class TX, class TT, class TZ, int LG, int EPI>
 __global__ void __launch_bounds__(OP_THREADS)
 k_vertex_rows(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
+              const SmallTerms<typename AccOf<TX>::type> sm,
               const typename AccOf<TX>::type* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
               int64_t ldx, TZ* __restrict__ Z, int64_t ldz, int c0, int cw, int c, double a, double b,
               const double* __restrict__ Y, int64_t ldy, double gy, double* __restrict__ partials,
@@ -417,12 +450,24 @@ k_vertex_rows(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __r
         for (int j = 0; j < E; ++j) acc[j] += x[j];
       }
     }
+    // small hyperedges: the other members' rows of X, weighted by t_e s_nb
+    for (int64_t k2 = __ldg(sm.ptr + v), kend = __ldg(sm.ptr + v + 1); k2 < kend; ++k2) {
+      const int32_t u = __ldg(sm.nb + k2);
+      const A cf = __ldg(sm.coef + k2);
+      if (active) {
+        A x[E];
+        vload<A, TX, E>(X + (int64_t)u * ldx + c0 + col, x);
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[j] = fma(cf, x[j], acc[j]);
+      }
+    }
     if (active) {
       const A sb = bb * (A)__ldg(s + v);
+      const A ad = aa + bb * __ldg(sm.diag + v);
       A x[E], z[E];
       vload<A, TX, E>(X + v * ldx + c0 + col, x);
 #pragma unroll
-      for (int j = 0; j < E; ++j) z[j] = fma(aa, x[j], sb * acc[j]);
+      for (int j = 0; j < E; ++j) z[j] = fma(ad, x[j], sb * acc[j]);
       if constexpr (EPI == EPI_RESID) {
         double y[E];
         const int nv = cw - col < E ? cw - col : E;

@@ -142,6 +142,40 @@ def test_apply_theta_low_precision(dtype, rtol, c):
     assert (err <= rtol * scale + 1e-30).all(), err.max()
 
 
+@pytest.mark.parametrize("sizes", ["small", "large", "mixed"])
+@pytest.mark.parametrize("dtype,rtol", [(torch.float64, 1e-12), (torch.float32, 2e-6), (torch.bfloat16, 1.2e-2)])
+def test_apply_theta_small_and_large_hyperedges(sizes, dtype, rtol):
+    """Hyperedges of at most three members (one-member ones included) enter the vertex
+    pass straight from X, larger ones go through the intermediate: graphs with only
+    small, only large, or both kinds (plus a heavy hyperedge and vertices in no
+    hyperedge) match Eq. 1 in the oracle."""
+    rng = np.random.default_rng({"small": 1, "large": 2, "mixed": 3}[sizes])
+    n, m, c = 3000, 5000, 37
+    if sizes == "small":
+        sz = rng.integers(1, 4, m)
+    elif sizes == "large":
+        sz = rng.integers(4, 12, m)
+    else:
+        sz = rng.integers(1, 7, m)
+        sz[7] = 400
+    members = np.concatenate([rng.choice(n - 50, int(k), replace=False) for k in sz]).astype(np.int32)
+    edge_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(sz, out=edge_ptr[1:])
+    H = incidence.incidence_matrix(incidence.build_incidence(n, m, edge_ptr, members))
+    w = rng.random(m) + 0.01
+    g = hgl.build_incidence(n, m, edge_ptr, members)
+    Xt = _panel(rng.standard_normal((n, c)), dtype)
+    X = Xt.to(torch.float64).cpu().numpy()
+    Z = hgl.apply_theta(g, torch.tensor(w, device=DEV), Xt, 1.5, -1.0)
+    ref = core.theta_apply(H, w, X, 1.5, -1.0)
+    err = np.abs(Z.to(torch.float64).cpu().numpy() - ref)
+    scale = np.abs(ref) + np.abs(1.5 * X) + core.theta_apply(H, w, np.abs(X), 0.0, 1.0)
+    assert (err <= rtol * scale + 1e-30).all(), err.max()
+    # the last 50 vertices are in no hyperedge: Z = 1.5 X there (exact in FP64)
+    if dtype == torch.float64:
+        assert np.array_equal(Z.cpu().numpy()[-50:], 1.5 * X[-50:])
+
+
 @pytest.mark.parametrize("dtype,ch", [(hgl.HGL_FP64, torch.float64), (hgl.HGL_FP32, torch.float32)])
 def test_tuned_operator_and_residual_still_match(dtype, ch):
     """Tuning only changes the column chunk: results stay within each path's bound."""
