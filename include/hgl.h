@@ -107,6 +107,19 @@ hgl_status hgl_profile_read(int32_t family, double* ms_total, int64_t* launches)
  */
 hgl_status hgl_selftest_wait_timeout(int64_t limit_cycles, void* stream);
 
+/*
+ * hgl_selftest_pair_split -- the conversions between an FP64 panel and the FP32 pair
+ * (hi, lo) that the mixed-precision solver keeps its iterate in (refinement around an
+ * FP32 CG; the benchmark spec's FP64 residual recomputation), run on given values: for each
+ * i, hi[i] = x[i] rounded to FP32 (nearest-even), lo[i] = x[i] - hi[i] rounded to FP32,
+ * back[i] = (double)hi[i] + (double)lo[i] in FP64.  The solver computes these from the
+ * IEEE-754 bit fields (no FP64 arithmetic in range) and this call exposes them for a test
+ * against the plain FP64 definitions.
+ *   x     device FP64[len];  hi, lo  device FP32[len];  back  device FP64[len]
+ * Asynchronous on `stream`.  Errors: HGL_ERR_INVALID_ARG (NULL arrays, len < 0).
+ */
+hgl_status hgl_selftest_pair_split(const double* x, int64_t len, float* hi, float* lo, double* back, void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Incidence (Section 2: H(v,e) = 1 iff v in e; de(e) = sum_v H(v,e))         */
 /* ------------------------------------------------------------------------- */

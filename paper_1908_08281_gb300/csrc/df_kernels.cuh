@@ -37,6 +37,49 @@ __device__ __forceinline__ f2 split(double x) {
   return r;
 }
 
+// ---- conversions between FP64 and the FP32 pair without FP64 arithmetic ----
+// The panels are converted at the start and end of every mixed-precision solve; with
+// the FP64 pipe ~58x slower than FP32, three or four FP64 operations per element made
+// those passes FP64-bound.  These work on the IEEE-754 binary64 / binary32 bit fields
+// and give the same results as the FP64 conversions; values outside the fast range
+// (zero, subnormal, very large or small, infinite, NaN) take the FP64 conversions.
+
+// split(x) from the bits: hi = x rounded to nearest-even at 24 significant bits, lo = the
+// exact remainder (an integer of at most 29 bits times 2^(e-52)) rounded to FP32.
+__device__ __forceinline__ f2 split_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7FF) - 1023;
+  if (e < -70 || e > 120) return split(x);
+  const unsigned long long M = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  unsigned long long H = M >> 29;
+  const unsigned long long rem = M & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rem > half || (rem == half && (H & 1ull))) ++H;
+  const long long R = (long long)M - (long long)(H << 29);  // |R| <= 2^28
+  int eh = e;
+  if (H == (1ull << 24)) {  // the rounding carried into the next binade
+    H >>= 1;
+    ++eh;
+  }
+  const unsigned sign = (unsigned)(u >> 63) << 31;
+  f2 r;
+  r.hi = __uint_as_float(sign | ((unsigned)(eh + 127) << 23) | (unsigned)(H & 0x7FFFFFull));
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);  // 2^(e-52), a normal float
+  const float lo = __int2float_rn((int)R) * scale;                         // exact scaling
+  r.lo = R == 0 ? 0.f : (sign ? -lo : lo);
+  return r;
+}
+
+// (double)f from the bits (exact).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+  const unsigned eb = (b >> 23) & 0xFFu;
+  if ((b & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)s);
+  if (eb == 0 || eb == 0xFFu) return (double)f;
+  return __longlong_as_double(
+      (long long)(s | ((unsigned long long)(eb + 896u) << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 // acc += a * b
 __device__ __forceinline__ void fma2(f2& acc, f2 a, f2 b) {
   const float p = __fmul_rn(a.hi, b.hi);
@@ -269,7 +312,7 @@ __global__ void k_split_vec(int64_t len, const double* __restrict__ x, float* __
 
 // (Fh, Fl) <- F (FP64 panel), or (Fh, Fl) += D (FP32 panel), or F <- Fh + Fl.
 // With Fl16, SPLIT and ACCUMULATE also store the low part rounded to BF16 (the copy the
-// compact residual gathers).  One thread per 4-column vector of a row.
+// compact residual gathers).  One warp per row.
 enum PanelOp : int { SPLIT = 0, ACCUMULATE = 1, COMBINE = 2 };
 
 template <int OP>
@@ -278,42 +321,65 @@ __global__ void k_panel(int64_t n, int c, double* __restrict__ F, int64_t ldf, f
                         const int32_t* __restrict__ guard, bf16_t* __restrict__ Fl16, int64_t ld16) {
   if (guard && *guard == 0) return;
   const int vecs = (c + 3) / 4;
-  const int64_t total = n * vecs;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = q / vecs;
-    const int col = (int)(q % vecs) * 4;
-    const int nv = c - col < 4 ? c - col : 4;
-    float h[4], lo[4];
-    if (OP == SPLIT) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // one warp per row, lanes over its 4-column vectors (coalesced; FP64 rows read and
+  // written as 2 x 16 bytes per vector: ldf * 8 is a multiple of 16 and col of 4)
+  for (int64_t r = warp; r < n; r += nwarps) {
+    for (int vi = lane; vi < vecs; vi += 32) {
+      const int col = vi * 4;
+      const int nv = c - col < 4 ? c - col : 4;
+      float h[4], lo[4];
+      if (OP == SPLIT) {
+        double x[4] = {0.0, 0.0, 0.0, 0.0};
+        if (nv == 4) {
+          const double2 a = reinterpret_cast<const double2*>(F + r * ldf + col)[0];
+          const double2 b = reinterpret_cast<const double2*>(F + r * ldf + col)[1];
+          x[0] = a.x;
+          x[1] = a.y;
+          x[2] = b.x;
+          x[3] = b.y;
+        } else {
+          for (int j = 0; j < nv; ++j) x[j] = F[r * ldf + col + j];
+        }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const f2 x = split(j < nv ? F[r * ldf + col + j] : 0.0);
-        h[j] = x.hi;
-        lo[j] = x.lo;
-      }
-      vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
-      vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
-      if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
-    } else if (OP == ACCUMULATE) {
-      float d[4];
-      vload<float, float, 4, false>(Fh + r * ld32 + col, h);
-      vload<float, float, 4, false>(Fl + r * ld32 + col, lo);
-      vload<float, float, 4, false>(D + r * ld32 + col, d);
+        for (int j = 0; j < 4; ++j) {
+          const f2 y = split_bits(x[j]);
+          h[j] = y.hi;
+          lo[j] = y.lo;
+        }
+        vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
+        vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
+        if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
+      } else if (OP == ACCUMULATE) {
+        float d[4];
+        vload<float, float, 4, false>(Fh + r * ld32 + col, h);
+        vload<float, float, 4, false>(Fl + r * ld32 + col, lo);
+        vload<float, float, 4, false>(D + r * ld32 + col, d);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (j >= nv) d[j] = 0.f;  // columns past c are padding
-        f2 x{h[j], lo[j]};
-        add2(x, f2{d[j], 0.f});
-        h[j] = x.hi;
-        lo[j] = x.lo;
+        for (int j = 0; j < 4; ++j) {
+          if (j >= nv) d[j] = 0.f;  // columns past c are padding
+          f2 x{h[j], lo[j]};
+          add2(x, f2{d[j], 0.f});
+          h[j] = x.hi;
+          lo[j] = x.lo;
+        }
+        vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
+        vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
+        if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
+      } else {
+        vload<float, float, 4, false>(Fh + r * ld32 + col, h);
+        vload<float, float, 4, false>(Fl + r * ld32 + col, lo);
+        if (nv == 4) {
+          reinterpret_cast<double2*>(F + r * ldf + col)[0] =
+              make_double2(f2d_bits(h[0]) + f2d_bits(lo[0]), f2d_bits(h[1]) + f2d_bits(lo[1]));
+          reinterpret_cast<double2*>(F + r * ldf + col)[1] =
+              make_double2(f2d_bits(h[2]) + f2d_bits(lo[2]), f2d_bits(h[3]) + f2d_bits(lo[3]));
+        } else {
+          for (int j = 0; j < nv; ++j) F[r * ldf + col + j] = f2d_bits(h[j]) + f2d_bits(lo[j]);
+        }
       }
-      vstore<float, float, 4>(Fh + r * ld32 + col, h, 4);
-      vstore<float, float, 4>(Fl + r * ld32 + col, lo, 4);
-      if (Fl16) vstore<bf16_t, float, 4>(Fl16 + r * ld16 + col, lo, 4);
-    } else {
-      vload<float, float, 4, false>(Fh + r * ld32 + col, h);
-      vload<float, float, 4, false>(Fl + r * ld32 + col, lo);
-      for (int j = 0; j < nv; ++j) F[r * ldf + col + j] = (double)h[j] + (double)lo[j];
     }
   }
 }

@@ -1,6 +1,6 @@
 // resid_df.cu -- launches of the pair-arithmetic residual (df_kernels.cuh): the
 // mixed-precision solver keeps its FP64 iterate F as two FP32 panels (hi, lo) and
-// recomputes lam Y - M F from them to ~48 significant bits.
+// recomputes lam Y - M F from them to ~48 significant bits; hgl_selftest_pair_split.
 #include <algorithm>
 
 #include "df_kernels.cuh"
@@ -44,7 +44,7 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
   constexpr int E = 4;
   const int nvec = (c + E - 1) / E;
   int lg = 1, nv = 1;
-  const int tuned = tuned_chunk_vecs(g, TUNE_PAIR, c);
+  const int tuned = tuned_chunk_vecs(g, Fl16 ? TUNE_PAIR16 : TUNE_PAIR, c);
   pick_tile(std::min(nvec, tuned > 0 ? tuned : 32), &lg, &nv);
   const int cc = lg * nv * E;
   hgl_status stt = HGL_OK;
@@ -88,7 +88,7 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
     if (false) {
     }
     HGL_DF_CASE(1, 1) HGL_DF_CASE(2, 1) HGL_DF_CASE(4, 1) HGL_DF_CASE(8, 1) HGL_DF_CASE(16, 1) HGL_DF_CASE(32, 1)
-    HGL_DF_CASE(32, 2)
+    HGL_DF_CASE(32, 2) HGL_DF_CASE(32, 4)
 #undef HGL_DF_CASE
 #undef HGL_DF_LAUNCH
     HGL_CHECK_CUDA(cudaGetLastError());
@@ -97,4 +97,31 @@ hgl_status df_residual(hgl_graph* g, const float* s_hi, const float* s_lo, const
   return HGL_OK;
 }
 
+namespace {
+
+__global__ void k_pair_selftest(int64_t len, const double* __restrict__ x, float* __restrict__ hi,
+                                float* __restrict__ lo, double* __restrict__ back) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const df::f2 p = df::split_bits(x[i]);
+    hi[i] = p.hi;
+    lo[i] = p.lo;
+    back[i] = df::f2d_bits(p.hi) + df::f2d_bits(p.lo);
+  }
+}
+
+}  // namespace
 }  // namespace hgl
+
+// The solver's FP64 <-> FP32-pair conversions on given values (a test of the bit-field
+// conversions against their FP64 definitions).
+extern "C" hgl_status hgl_selftest_pair_split(const double* x, int64_t len, float* hi, float* lo, double* back,
+                                              void* stream) {
+  if (len < 0 || (len > 0 && (!x || !hi || !lo || !back)))
+    return hgl::record_error(HGL_ERR_INVALID_ARG, "NULL array or negative length");
+  if (len == 0) return HGL_OK;
+  cudaStream_t st = hgl::as_stream(stream);
+  hgl::count_launch();
+  hgl::k_pair_selftest<<<(unsigned)std::min<int64_t>((len + 255) / 256, 4096), 256, 0, st>>>(len, x, hi, lo, back);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  return HGL_OK;
+}

@@ -57,9 +57,15 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
   const int E = (int)(16 / elt);
   const int64_t ld = (c + E - 1) / E * E;
   const int nvec = (c + E - 1) / E;
-  DevMem X, Z;
+  // the variant the CG iteration launches: Z = M X with the column partials of X.Z,
+  // Z in FP32 for BF16 search directions
+  const int zdt = dtype == HGL_BF16 ? HGL_FP32 : dtype;
+  const size_t zelt = dtype_size(zdt);
+  const int64_t ldz = (c + (int)(16 / zelt) - 1) / (int)(16 / zelt) * (int)(16 / zelt);
+  DevMem X, Z, part;
   HGL_CHECK_CUDA(cudaMalloc(&X.p, elt * (size_t)g->n * ld));
-  HGL_CHECK_CUDA(cudaMalloc(&Z.p, elt * (size_t)g->n * ld));
+  HGL_CHECK_CUDA(cudaMalloc(&Z.p, zelt * (size_t)g->n * ldz));
+  HGL_CHECK_CUDA(cudaMalloc(&part.p, sizeof(double) * (size_t)op_partial_rows(g) * c));
   HGL_CHECK_CUDA(cudaMemsetAsync(X.p, 0x3F, elt * (size_t)g->n * ld, st));  // finite, normal values
 
   // operator apply: chunk widths of 1 .. 128 vectors per row (each a distinct tile;
@@ -71,15 +77,16 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
     OpCall cl{};
     cl.g = g;
     cl.xdt = dtype;
-    cl.zdt = dtype;
+    cl.zdt = zdt;
     cl.X = X.p;
     cl.ldx = ld;
     cl.Z = Z.p;
-    cl.ldz = ld;
+    cl.ldz = ldz;
     cl.c = c;
     cl.a = 1.5;
     cl.b = -1.0;
-    cl.epi = EPI_PLAIN;
+    cl.epi = EPI_DOT_XZ;
+    cl.partials = static_cast<double*>(part.p);
     cl.chunk_cols = cand * E;
     float ms = 0.f;
     HGL_TRY(time_ms(st, [&] { return op_launch(cl, st, nullptr); }, &ms));
@@ -92,23 +99,20 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
   g->tuned_chunk[tune_key(dtype, c)] = best;
   if (chunk_cols) *chunk_cols = best * E;
   // grid policy at that chunk: the blocks resident at once (one wave) or eight per SM,
-  // timed with the epilogue the CG iteration uses (Z and the column partials of X.Z;
-  // BF16 panels, whose CG writes FP32 Z, with the plain epilogue)
+  // timed with the same variant
   {
-    DevMem part;
-    HGL_CHECK_CUDA(cudaMalloc(&part.p, sizeof(double) * (size_t)op_partial_rows(g) * c));
     OpCall cl{};
     cl.g = g;
     cl.xdt = dtype;
-    cl.zdt = dtype;
+    cl.zdt = zdt;
     cl.X = X.p;
     cl.ldx = ld;
     cl.Z = Z.p;
-    cl.ldz = ld;
+    cl.ldz = ldz;
     cl.c = c;
     cl.a = 1.5;
     cl.b = -1.0;
-    cl.epi = dtype == HGL_BF16 ? EPI_PLAIN : EPI_DOT_XZ;
+    cl.epi = EPI_DOT_XZ;
     cl.partials = static_cast<double*>(part.p);
     // the two grids are often within a few percent: alternate them three times, keep
     // each one's best time, and leave the one-wave default unless eight per SM wins
@@ -145,27 +149,35 @@ extern "C" hgl_status hgl_tune_operator(hgl_graph* g, const double* w, int32_t c
     float* t_hi = s_lo + g->n;
     float* t_lo = t_hi + g->m;
     HGL_TRY(df_split_scalings(g, s_hi, s_lo, t_hi, t_lo, st));
-    int pbest = 0;
-    float pbest_ms = 0.f;
-    const uint64_t key = tune_key(TUNE_PAIR, c);
-    for (int vecs : {8, 16, 32, 64}) {
-      const int cand = std::min(vecs, pvec);
-      g->tuned_chunk[key] = cand;
-      float ms = 0.f;
-      int r_rows = 0;
-      HGL_TRY(time_ms(st, [&] {
-        return df_residual(g, s_hi, s_lo, t_hi, t_lo, static_cast<float*>(Fh.p), static_cast<float*>(Fl.p), ld32,
-                           static_cast<double*>(Y.p), ld64, -1.5, 1.0, 0.5, c, static_cast<float*>(R.p),
-                           static_cast<double*>(part.p), st, &r_rows);
-      }, &ms));
-      if (pbest == 0 || ms < pbest_ms) {
-        pbest = cand;
-        pbest_ms = ms;
+    // both variants: the full pair and the compact one (F's low part gathered in BF16)
+    const int64_t ld16 = (c + 7) / 8 * 8;
+    DevMem Fl16;
+    HGL_CHECK_CUDA(cudaMalloc(&Fl16.p, 2 * (size_t)g->n * ld16));
+    HGL_CHECK_CUDA(cudaMemsetAsync(Fl16.p, 0, 2 * (size_t)g->n * ld16, st));
+    for (int variant = 0; variant < 2; ++variant) {
+      const bf16_t* lo16 = variant ? static_cast<const bf16_t*>(Fl16.p) : nullptr;
+      int pbest = 0;
+      float pbest_ms = 0.f;
+      const uint64_t key = tune_key(variant ? TUNE_PAIR16 : TUNE_PAIR, c);
+      for (int vecs : {8, 16, 32, 64, 128}) {
+        const int cand = std::min(vecs, pvec);
+        g->tuned_chunk[key] = cand;
+        float ms = 0.f;
+        int r_rows = 0;
+        HGL_TRY(time_ms(st, [&] {
+          return df_residual(g, s_hi, s_lo, t_hi, t_lo, static_cast<float*>(Fh.p), static_cast<float*>(Fl.p), ld32,
+                             static_cast<double*>(Y.p), ld64, -1.5, 1.0, 0.5, c, static_cast<float*>(R.p),
+                             static_cast<double*>(part.p), st, &r_rows, nullptr, nullptr, 0, nullptr, lo16, ld16);
+        }, &ms));
+        if (pbest == 0 || ms < pbest_ms) {
+          pbest = cand;
+          pbest_ms = ms;
+        }
+        if (cand == pvec) break;
       }
-      if (cand == pvec) break;
+      g->tuned_chunk[key] = pbest;
+      if (pair_chunk_cols && variant == 0) *pair_chunk_cols = pbest * 4;
     }
-    g->tuned_chunk[key] = pbest;
-    if (pair_chunk_cols) *pair_chunk_cols = pbest * 4;
   } else if (pair_chunk_cols) {
     *pair_chunk_cols = 0;
   }

@@ -108,13 +108,16 @@ k_panel_scale(int64_t n, int c, const TX* __restrict__ X, int64_t ldx, double sc
   const int col0 = blockIdx.y * L::TILE;
   const int col = col0 + l * E;
   DotAcc<Acc> d[E];
+  // a unit scale is a plain copy (no FP64 conversions on FP32 panels)
+  const bool unit = scale == 1.0;
   if (col < c) {
     const int64_t rstep = (int64_t)gridDim.x * (VEC_THREADS / 32) * L::G;
     for (int64_t r = ((int64_t)blockIdx.x * (VEC_THREADS / 32) + wid) * L::G + grp; r < n; r += rstep) {
       Acc x[E];
       vload<Acc, TX, E>(X + r * ldx + col, x);
+      if (!unit)
 #pragma unroll
-      for (int j = 0; j < E; ++j) x[j] = (Acc)(scale * (double)x[j]);
+        for (int j = 0; j < E; ++j) x[j] = (Acc)(scale * (double)x[j]);
       vstore<TZ, Acc, E>(Z + r * ldz + col, x, c - col);
       if (DOT) {
 #pragma unroll

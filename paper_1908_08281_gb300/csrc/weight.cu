@@ -207,16 +207,22 @@ __global__ void k_grad_final(int64_t m, const int64_t* __restrict__ csc_ptr, con
                              const int32_t* __restrict__ de, const double* __restrict__ ex,
                              const double* __restrict__ phi, const double* __restrict__ w, double mu,
                              double theta_sign, double* __restrict__ grad) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t e = warp; e < m; e += nwarps) {
+  // groups of 8 lanes per hyperedge (most hyperedges have a few members), a fixed
+  // lane-to-member assignment and a fixed butterfly: the sum order depends on nothing
+  // but the hyperedge
+  constexpr int GL = 8;
+  const int sub = threadIdx.x % GL;
+  const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / GL;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / GL;
+  const int64_t rounds = (m + ngrp - 1) / ngrp;  // every lane runs the same number of rounds
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t e = grp + r * ngrp;
     double acc = 0.0;
-    if (phi)
-      for (int64_t i = csc_ptr[e] + lane, end = csc_ptr[e + 1]; i < end; i += 32) acc += phi[csc_idx[i]];
+    if (phi && e < m)
+      for (int64_t i = csc_ptr[e] + sub, end = csc_ptr[e + 1]; i < end; i += GL) acc += phi[csc_idx[i]];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) grad[e] = -theta_sign * (ex[e] / (double)de[e] - acc) + 2.0 * mu * w[e];
+    for (int o = GL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (sub == 0 && e < m) grad[e] = -theta_sign * (ex[e] / (double)de[e] - acc) + 2.0 * mu * w[e];
   }
 }
 

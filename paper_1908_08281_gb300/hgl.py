@@ -95,6 +95,7 @@ _SIGNATURES = {
     "hgl_tune_block_rsvd": (_I32, [_P, _P, ctypes.POINTER(_I64), _I32, _I32, _I32, _I32, ctypes.POINTER(_I32),
                                    ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
+    "hgl_selftest_pair_split": (_I32, [_P, _I64, _P, _P, _P, _P]),
     "hgl_block_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
@@ -436,6 +437,20 @@ def tune_block_rsvd(g: Graph, w: torch.Tensor, block_ptr, k: int, p: int, q: int
     _check(lib().hgl_tune_block_rsvd(g.handle, _vec(w, "w"), bp, len(block_ptr) - 1, k, p, q, ctypes.byref(route),
                                      ctypes.byref(md), ctypes.byref(ms), _stream(stream)))
     return route.value, md.value, ms.value
+
+
+def selftest_pair_split(x: torch.Tensor, stream=None):
+    """(hi, lo, back) of the mixed solver's FP64 <-> FP32-pair conversions on x (FP64)."""
+    x = x.contiguous()
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise ValueError("x must be a CUDA float64 tensor")
+    hi = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    lo = torch.empty_like(hi)
+    back = torch.empty_like(x)
+    _check(lib().hgl_selftest_pair_split(ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(hi.data_ptr()),
+                                         ctypes.c_void_p(lo.data_ptr()), ctypes.c_void_p(back.data_ptr()),
+                                         _stream(stream)))
+    return hi, lo, back
 
 
 def selftest_wait_timeout(limit_cycles: int, stream=None):

@@ -273,6 +273,35 @@ def test_cg_fp32_loose_tol_starts_from_fp32_residual():
     assert np.array_equal(F2.cpu().numpy(), Fg)
 
 
+def test_pair_split_conversions_match_fp64_definitions():
+    """The mixed solver's FP64 <-> FP32-pair conversions (computed from the IEEE-754 bit
+    fields, no FP64 arithmetic in range) equal their plain definitions bit for bit:
+    hi = fl32(x), lo = fl32(x - hi), back = hi + lo in FP64 -- over random magnitudes,
+    rounding ties, significands that carry into the next binade, signed zeros,
+    subnormals, values outside the fast range, infinities and NaN."""
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal(200000) * 10.0 ** rng.uniform(-25, 35, 200000)
+    f = rng.standard_normal(5000).astype(np.float32).astype(np.float64)
+    ulp = np.spacing(f.astype(np.float32)).astype(np.float64)
+    special = np.concatenate([
+        f + 0.5 * ulp, f - 0.5 * ulp,               # ties (rounded to even)
+        f + 0.5 * ulp * (1 + 2.0 ** -20),           # just above a tie
+        np.nextafter(2.0 ** np.arange(-60, 60), 0),  # all-ones significands: the rounding carries
+        [0.0, -0.0, 5e-324, -2.2e-308, 1e-30, 3e-22, 1e38, 3.4e38, 1e40, -1e300, np.inf, -np.inf, np.nan],
+    ])
+    x = np.concatenate([x, special])
+    hi, lo, back = hgl.selftest_pair_split(torch.tensor(x, device=DEV))
+    with np.errstate(over="ignore", invalid="ignore"):
+        rhi = x.astype(np.float32)
+        rlo = (x - rhi.astype(np.float64)).astype(np.float32)
+        rback = rhi.astype(np.float64) + rlo.astype(np.float64)
+    for got, ref in ((hi.cpu().numpy(), rhi), (lo.cpu().numpy(), rlo), (back.cpu().numpy(), rback)):
+        both_nan = np.isnan(got) & np.isnan(ref)
+        bits = np.uint32 if got.dtype == np.float32 else np.uint64
+        same = got.view(bits) == ref.view(bits)
+        assert (same | both_nan).all(), (x[~(same | both_nan)][:5], got[~(same | both_nan)][:5], ref[~(same | both_nan)][:5])
+
+
 def test_cg_zero_column_warm_start_and_ragged_c():
     wl, d, og, H = _case("small_fp64", 3, n=700, m=1000, c=7)
     w = np.full(d["m"], 1.0 / d["m"])
