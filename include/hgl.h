@@ -255,7 +255,7 @@ typedef struct {
                        /* the search directions stored in BF16 (the operator's input;    */
                        /* its product, the residual and the iterate stay FP32)           */
   double  inner_tol;   /* mixed modes: floor of the relative reduction asked of each     */
-                       /* inner solve; a sweep aims at max(inner_tol, 0.5 tol/relres)    */
+                       /* inner solve; a sweep aims at max(inner_tol, 0.75 tol/relres)   */
                        /* (0 = 1e-5)                                                     */
   int32_t max_refine;  /* mixed modes: cap on refinement sweeps (0 = 8)                  */
   int32_t flags;       /* HGL_SOLVE_WARM_START                                           */
@@ -431,6 +431,16 @@ hgl_status hgl_schur_inverse(const hgl_graph* g, const double* w, double lam, in
 
 /* Release a preconditioner (NULL is a no-op). */
 void hgl_precond_destroy(hgl_precond* P);
+
+/*
+ * hgl_step_precond -- the block-rSVD preconditioner (Section 3, Algorithm 1 on the
+ * diagonal blocks, used as in Eq. 15) that the graph's captured adaptive step
+ * (HGL_STEP_GRAPH, route HGL_ROUTE_BR) built in its last call, at that call's w before
+ * the weight step.  The handle stays owned by the graph: read it (hgl_precond_export,
+ * hgl_precond_apply) until the next hgl_adaptive_step call or hgl_graph_destroy, and do
+ * not destroy it.  Errors: HGL_ERR_INVALID_ARG (no captured BR step on this graph).
+ */
+hgl_status hgl_step_precond(const hgl_graph* g, const hgl_precond** out);
 
 /*
  * hgl_precond_export -- copy block b's factors to caller-owned DEVICE FP64 arrays:

@@ -91,14 +91,16 @@ __global__ void k_set_target(CgState S, double tol2) {
 
 // Inner-solve targets of a refinement sweep: columns already at tol are frozen
 // (target +inf); the others aim at rr_inner <= rel^2 rr_true, rel = max(inner_tol,
-// INNER_MARGIN tol / relres): half of what the outer tolerance still needs.  The
-// other half covers what the recursive FP32 residual does not see -- the rounding of
-// the correction and of F's FP32 pair (a few units of 2^-24 of ||lam Y||), and the
-// error of an FP32 first-residual estimate -- so that another sweep (a pair-arithmetic
-// residual and a CG restart) is rarely needed, without solving past the tolerance.
-// Also sets *S.need = 1 when some column needs the sweep (captured solves zero it
-// before this kernel and guard the sweep's expensive launches with it).
-constexpr double INNER_MARGIN = 0.5;
+// INNER_MARGIN tol / relres): three quarters of what the outer tolerance still needs.
+// The last quarter covers what the recursive FP32 residual does not see -- the
+// rounding of the correction and of F's FP32 pair (a few units of 2^-24 of ||lam Y||),
+// and the error of an FP32 first-residual estimate -- so that another sweep (a
+// pair-arithmetic residual and a CG restart) is rarely needed, without solving past
+// the tolerance (measured at n = 1M, c = 512, tol 3e-6: final relres at most 2.25e-6,
+// no second sweep in 20 outer iterations; a half margin took 0.25 more iterations per
+// solve).  Also sets *S.need = 1 when some column needs the sweep (captured solves zero
+// it before this kernel and guard the sweep's expensive launches with it).
+constexpr double INNER_MARGIN = 0.75;
 
 __global__ void k_inner_targets(CgState S, double tol, double inner_tol) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < S.c; j += gridDim.x * blockDim.x) {

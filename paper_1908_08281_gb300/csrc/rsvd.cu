@@ -106,6 +106,11 @@ struct Work {
   int32_t* fail = nullptr;
   int* err = nullptr;
   bool sparse = false;    // Theta_bb S from the incidence lists (no dense blocks)
+  // kept pattern of the dense blocks (plans with their own space): per storage row the
+  // segments of in-block members, found once; builds clear and refill only those
+  int64_t* seg_ptr = nullptr;
+  rsvd::Segment* seg = nullptr;
+  bool kept = false;
 };
 
 inline size_t a256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -316,6 +321,7 @@ struct PrecondPlan {
   Work wk;
   hgl_precond* P = nullptr;
   Buffer own;            // the plan's own work space (graph plans); else g->rsvd
+  Buffer pattern;        // kept pattern of the dense blocks (own-space BF16 plans)
   int dtype = HGL_BF16;
   int q = 0;
 };
@@ -366,10 +372,48 @@ static hgl_status block_route_sparse(hgl_graph* g, const int64_t* bp, int nb, cu
   return HGL_OK;
 }
 
+// The dense blocks' pattern of an own-space plan: segment counts per storage row, their
+// offsets (scanned on the host, once), the segments; then the block storage zeroed once.
+// Synchronous.
+static hgl_status keep_pattern(hgl_graph* g, PrecondPlan* pl, cudaStream_t st) {
+  Work& wk = pl->wk;
+  const int64_t rows = wk.rows_tot;
+  void* tmp = nullptr;
+  HGL_CHECK_CUDA(cudaMalloc(&tmp, sizeof(unsigned) * (size_t)rows));
+  std::vector<unsigned> cnt(rows);
+  hgl::count_launch();
+  rsvd::k_segment_count<<<g->num_sms * 8, 256, 0, st>>>(wk.B, rows, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx,
+                                                        static_cast<unsigned*>(tmp));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), tmp, sizeof(unsigned) * (size_t)rows, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_error(e, "block pattern count", __FILE__, __LINE__);
+  std::vector<int64_t> ptr(rows + 1, 0);
+  for (int64_t r = 0; r < rows; ++r) ptr[r + 1] = ptr[r] + cnt[r];
+  const size_t ptr_bytes = (sizeof(int64_t) * (size_t)(rows + 1) + 255) & ~size_t(255);
+  hgl_status s = HGL_OK;
+  char* base = static_cast<char*>(
+      buffer_get(pl->pattern, ptr_bytes + sizeof(rsvd::Segment) * (size_t)std::max<int64_t>(ptr[rows], 1), &s));
+  if (!base) return s;
+  wk.seg_ptr = reinterpret_cast<int64_t*>(base);
+  wk.seg = reinterpret_cast<rsvd::Segment*>(base + ptr_bytes);
+  HGL_CHECK_CUDA(cudaMemcpyAsync(wk.seg_ptr, ptr.data(), sizeof(int64_t) * (size_t)(rows + 1), cudaMemcpyHostToDevice, st));
+  hgl::count_launch();
+  rsvd::k_segment_fill<<<g->num_sms * 8, 256, 0, st>>>(wk.B, rows, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx,
+                                                       wk.seg_ptr, wk.seg);
+  HGL_CHECK_CUDA(cudaGetLastError());
+  HGL_CHECK_CUDA(cudaMemsetAsync(wk.A, 0, sizeof(__nv_bfloat16) * (size_t)rows * (size_t)wk.ldA, st));
+  HGL_CHECK_CUDA(cudaStreamSynchronize(st));
+  wk.kept = true;
+  return HGL_OK;
+}
+
 void precond_plan_destroy(PrecondPlan* pl) {
   if (!pl) return;
   if (pl->P) hgl_precond_destroy(pl->P);
   buffer_free(pl->own);
+  buffer_free(pl->pattern);
   delete pl;
 }
 
@@ -393,6 +437,7 @@ hgl_status precond_plan_create(const hgl_graph* gc, double lam, const int64_t* b
     return s_;
   }
   s_ = plan(g, own_space ? pl->own : g->rsvd, bp, nb, k, l, lpad, gemm_dtype, sparse, &pl->wk);
+  if (s_ == HGL_OK && own_space && gemm_dtype == HGL_BF16 && !sparse) s_ = keep_pattern(g, pl, st);
   if (s_ != HGL_OK) {
     precond_plan_destroy(pl);
     return s_;
@@ -554,9 +599,14 @@ hgl_status precond_plan_compute(const hgl_graph* gc, PrecondPlan* pl, uint64_t s
     });
   } else if (bf16) {
     hgl::count_launch(2);
-    rsvd::k_assemble<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
-        wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->s32, g->t32,
-        static_cast<__nv_bfloat16*>(wk.A));
+    if (wk.kept)
+      rsvd::k_assemble_kept<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
+          wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_idx, wk.seg_ptr, wk.seg, g->s32, g->t32,
+          static_cast<__nv_bfloat16*>(wk.A));
+    else
+      rsvd::k_assemble<__nv_bfloat16, float><<<sms * 8, 256, 0, st>>>(
+          wk.B, wk.rows_tot, g->csr_ptr, g->csr_idx, g->csc_ptr, g->csc_idx, g->s32, g->t32,
+          static_cast<__nv_bfloat16*>(wk.A));
     rsvd::k_omega<__nv_bfloat16><<<sms * 8, 256, 0, st>>>(wk.B, seed, seed_dev,
                                                          static_cast<__nv_bfloat16*>(wk.St));
   } else {

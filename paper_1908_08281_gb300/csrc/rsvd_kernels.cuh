@@ -154,6 +154,132 @@ __global__ void k_assemble(Blocks B, int64_t rows_tot, const int64_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// The same blocks from a kept pattern.  Which members of which hyperedge fall inside a
+// block depends on the incidence and the block layout, not on w, so a plan finds them
+// once: per storage row, the segments (e, lo, hi) of the row vertex's hyperedges with
+// another member in the block, [lo, hi) the block's part of e's sorted member list.  A
+// build then clears only those entries (the rest of the storage is zero since the plan
+// was created) and adds the terms in the same order as k_assemble, so the blocks come
+// out identical, without zeroing the padded rows or searching the member lists.
+// ---------------------------------------------------------------------------
+struct Segment {
+  int32_t e, lo, hi;
+};
+
+// Segments of storage row r (CSR order of the row vertex's hyperedges), counted
+// (out == nullptr) or written to out; one warp per row.
+__device__ __forceinline__ unsigned row_segments(const Blocks& B, int64_t r, const int64_t* __restrict__ csr_ptr,
+                                                 const int32_t* __restrict__ csr_idx,
+                                                 const int64_t* __restrict__ csc_ptr,
+                                                 const int32_t* __restrict__ csc_idx, Segment* out) {
+  const int lane = threadIdx.x & 31;
+  const int b = find_block(B.arow, B.nb, r);
+  const int64_t i = r - B.arow[b];
+  const int bs = B.rows[b];
+  if (i >= bs) return 0;
+  const int64_t v0 = B.v0[b], u = v0 + i;
+  const int64_t beg = csr_ptr[u], end = csr_ptr[u + 1];
+  unsigned n = 0;
+  for (int64_t q0 = beg; q0 < end; q0 += 32) {
+    const int64_t q = q0 + lane;
+    int64_t lo = 0, hi = 0;
+    int32_t e = 0;
+    if (q < end) {
+      e = csr_idx[q];
+      int64_t a = csc_ptr[e], z = csc_ptr[e + 1];
+      const int64_t me = z;
+      while (a < z) {
+        const int64_t mid = (a + z) >> 1;
+        if (csc_idx[mid] < v0) a = mid + 1; else z = mid;
+      }
+      lo = a;
+      z = me;
+      while (a < z) {
+        const int64_t mid = (a + z) >> 1;
+        if (csc_idx[mid] < v0 + bs) a = mid + 1; else z = mid;
+      }
+      hi = a;
+    }
+    const bool keep = hi - lo > 1;
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (out && keep) {
+      const unsigned pos = n + __popc(mask & ((1u << lane) - 1u));
+      out[pos] = Segment{e, (int32_t)lo, (int32_t)hi};
+    }
+    n += __popc(mask);
+  }
+  return n;
+}
+
+static __global__ void k_segment_count(Blocks B, int64_t rows_tot, const int64_t* __restrict__ csr_ptr,
+                                const int32_t* __restrict__ csr_idx, const int64_t* __restrict__ csc_ptr,
+                                const int32_t* __restrict__ csc_idx, unsigned* __restrict__ count) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows_tot; r += nwarps) {
+    const unsigned n = row_segments(B, r, csr_ptr, csr_idx, csc_ptr, csc_idx, nullptr);
+    if ((threadIdx.x & 31) == 0) count[r] = n;
+  }
+}
+
+static __global__ void k_segment_fill(Blocks B, int64_t rows_tot, const int64_t* __restrict__ csr_ptr,
+                               const int32_t* __restrict__ csr_idx, const int64_t* __restrict__ csc_ptr,
+                               const int32_t* __restrict__ csc_idx, const int64_t* __restrict__ seg_ptr,
+                               Segment* __restrict__ seg) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows_tot; r += nwarps)
+    row_segments(B, r, csr_ptr, csr_idx, csc_ptr, csc_idx, seg + seg_ptr[r]);
+}
+
+template <class TA, class S>
+__global__ void k_assemble_kept(Blocks B, int64_t rows_tot, const int64_t* __restrict__ csr_ptr,
+                                const int32_t* __restrict__ csr_idx, const int32_t* __restrict__ csc_idx,
+                                const int64_t* __restrict__ seg_ptr, const Segment* __restrict__ seg,
+                                const S* __restrict__ s, const S* __restrict__ t, TA* __restrict__ A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < rows_tot; r += nwarps) {
+    const int b = find_block(B.arow, B.nb, r);
+    const int64_t i = r - B.arow[b];
+    if (i >= B.rows[b]) continue;
+    TA* row = A + r * B.ldA;
+    const int64_t v0 = B.v0[b];
+    const int64_t u = v0 + i;
+    const int64_t k0 = seg_ptr[r], k1 = seg_ptr[r + 1];
+    // clear the previous build's off-diagonal entries
+    for (int64_t k = k0; k < k1; ++k) {
+      const Segment sg = seg[k];
+      for (int64_t p = sg.lo + lane; p < sg.hi; p += 32) {
+        const int32_t v = csc_idx[p];
+        if (v != u) row[v - v0] = from_acc<TA>(S(0));
+      }
+    }
+    const S su = s[u];
+    S d = S(0);
+    for (int64_t q = csr_ptr[u] + lane, end = csr_ptr[u + 1]; q < end; q += 32) d += t[csr_idx[q]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    __syncwarp();
+    if (lane == 0) row[i] = from_acc<TA>(su * su * d);
+    __syncwarp();
+    for (int64_t k = k0; k < k1; ++k) {
+      const Segment sg = seg[k];
+      const S f = su * t[sg.e];
+      for (int64_t p = sg.lo + lane; p < sg.hi; p += 32) {
+        const int32_t v = csc_idx[p];
+        if (v != u) {
+          const int64_t j = v - v0;
+          row[j] = from_acc<TA>(to_acc<TA, S>(row[j]) + f * s[v]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sparse route for blocks that hold few of Theta's entries: Theta_bb S straight from
 // the incidence lists, without dense blocks.
 //   Theta_bb[u, u] = s_u^2 sum_{e ni u} t_e

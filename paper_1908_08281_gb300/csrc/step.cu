@@ -477,3 +477,13 @@ extern "C" hgl_status hgl_adaptive_step(hgl_graph* g, double* w, const hgl_step_
   HGL_TRY(hgl::check_panel(F, ldf, c, 8, "F"));
   return hgl::adaptive_step_impl(g, w, *opts, Y, ldy, F, ldf, c, stats, hgl::as_stream(stream));
 }
+
+extern "C" hgl_status hgl_step_precond(const hgl_graph* g, const hgl_precond** out) {
+  if (!g || !out) return hgl::record_error(HGL_ERR_INVALID_ARG, "graph or out is NULL");
+  *out = nullptr;
+  const hgl::StepGraph* sg = g->step_graph;
+  if (!sg || !sg->plan)
+    return hgl::record_error(HGL_ERR_INVALID_ARG, "no captured block-rSVD step has been set up on this graph");
+  *out = hgl::precond_plan_handle(sg->plan);
+  return HGL_OK;
+}

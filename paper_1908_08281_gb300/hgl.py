@@ -96,6 +96,7 @@ _SIGNATURES = {
                                    ctypes.POINTER(_D), ctypes.POINTER(_D), _P]),
     "hgl_selftest_wait_timeout": (_I32, [_I64, _P]),
     "hgl_selftest_pair_split": (_I32, [_P, _I64, _P, _P, _P, _P]),
+    "hgl_step_precond": (_I32, [_P, _P]),
     "hgl_block_cg_solve": (_I32, [_P, _P, _D, _P, _I64, _P, _I64, _I32, _I32, _D, _I32, _I32, _P, _P, _P]),
     "hgl_weight_grad": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, _D, _I32, _P, _P]),
     "hgl_project_simplex": (_I32, [_P, _P, _D, _I64, _P]),
@@ -234,9 +235,9 @@ class Precond:
         return self._h
 
     def close(self):
-        if self._h and self._h.value:
+        if self._h and self._h.value and not getattr(self, "borrowed", False):
             lib().hgl_precond_destroy(self._h)
-            self._h = ctypes.c_void_p(0)
+        self._h = ctypes.c_void_p(0)
 
     def __del__(self):
         try:
@@ -385,6 +386,16 @@ def block_rsvd(g: Graph, w: torch.Tensor, lam: float, block_ptr, k: int, p: int,
     _check(lib().hgl_block_rsvd(g.handle, _vec(w, "w"), lam, bp, len(block_ptr) - 1, k, p, q, seed, gemm_dtype,
                                 _stream(stream), ctypes.byref(out)))
     return Precond(out.value, block_ptr, k)
+
+
+def step_precond(g: Graph, block_ptr, k: int) -> Precond:
+    """The preconditioner the graph's captured block-rSVD step built in its last call
+    (owned by the graph: valid until the next adaptive_step call; never destroyed here)."""
+    h = ctypes.c_void_p()
+    _check(lib().hgl_step_precond(g.handle, ctypes.byref(h)))
+    P = Precond(h.value, block_ptr, k)
+    P.borrowed = True
+    return P
 
 
 def precond_export(P: Precond, b: int, stream=None):

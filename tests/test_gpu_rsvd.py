@@ -351,6 +351,39 @@ def test_captured_step_matches_oracle_each_step(route, dtype, tol):
     assert st.solve.relres_max <= tol
 
 
+def test_captured_step_keeps_block_pattern_and_matches_fresh_build():
+    """The captured step's block rSVD keeps the dense blocks' pattern from build to build
+    (which members share a block does not depend on w) and clears only the entries it
+    wrote: after steps that moved w and zeroed weights, its preconditioner equals a fresh
+    build by hgl_block_rsvd (dense route, every row zeroed) at the same w and seed,
+    factor for factor and bit for bit (Section 3, Algorithm 1)."""
+    wl, d, H, w, g = _setup(n=6000, m=10000, c=8, seed=21)
+    hgl.set_block_product(g, hgl.HGL_BLOCKS_DENSE)
+    bp = d["block_ptr"]
+    k, p, q = 16, 8, 2
+    wt = torch.tensor(d["w0"], device=DEV)
+    Y = _panel(d["Y"])
+    F = hgl.padded_panel(d["n"], d["c"])
+    compared = 0
+    for i in range(5):
+        w_before = wt.clone()
+        hgl.adaptive_step(g, wt, Y, F, wl.lam, 1e-3, 5e-3, tol=3e-6, dtype=hgl.HGL_BF16, route=hgl.HGL_ROUTE_BR,
+                          block_ptr=bp, k=k, p=p, q=q, seed=SEED + i, flags=hgl.HGL_STEP_GRAPH)
+        if i < 2:
+            continue  # eager call and capture; later calls replay the graph
+        Ps = hgl.step_precond(g, bp, k)
+        Pf = hgl.block_rsvd(g, w_before, wl.lam, bp, k, p, q, SEED + i, gemm_dtype=hgl.HGL_BF16)
+        for b in range(len(bp) - 1):
+            Qs, es = hgl.precond_export(Ps, b)
+            Qf, ef = hgl.precond_export(Pf, b)
+            assert torch.equal(es, ef), (i, b)
+            assert torch.equal(Qs, Qf), (i, b)
+        compared += 1
+        Pf.close()
+    assert compared == 3
+    assert int((wt == 0).sum()) > 0  # the steps zeroed weights: entries of the pattern went to 0
+
+
 def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs():
     """With eta = 0 the weights stay put, so from the second step on the warm-started F
     already meets tol and the captured solve skips its sweeps; at tol = 3e-6 it starts
