@@ -43,11 +43,11 @@ METRIC = "adaptive outer iterations/sec (rel err <= 1e-5)"
 UNIT = "iters/s"
 TOL = 3e-6          # relative residual; kappa(M) <= 3 at lam = 0.5 -> relative error <= 9e-6
 SEED = 20190822
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel family on
-# the full workload at a given column chunk, from one ncu capture of this bench
-# (profiles/operator_apply_full_adaptive.md, profiles/pair_residual_full_adaptive.md);
-# reported as roofline.traffic only for a run of that workload with that chunk.
-NCU_TRAFFIC_PER_LAUNCH = {("operator", "fp32", 128): 66.0e9, ("residual", "fp32", 128): 149.2e9}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per call of a kernel family on
+# the full workload at a given panel type and column chunk, from one ncu capture of this
+# bench (summarised under profiles/); reported as roofline.traffic only for a run of that
+# workload with that chunk.
+NCU_TRAFFIC_PER_LAUNCH = {("operator", "bf16", 256): 46.3e9}
 LOOP = 20           # outer iterations of one adaptive loop
 K_RANK, P_OVER, Q_ITERS = 64, 10, 2
 BCG_S, BCG_STEPS = 32, 4   # block CG comparator: columns per group, outer iterations timed
