@@ -219,14 +219,17 @@ hgl_status hgl_apply_theta_noalloc(const hgl_graph* g, const double* w, double a
  * the chunk of the FP64-accurate pair residual that the mixed-precision solvers use.
  * The paper has no counterpart: the chunk trades one long burst per gathered row
  * against re-reading the index arrays once per chunk, and the best width depends on
- * n, m, c, the panel type and the degree distribution.  At the chosen chunk it also
- * times the grid of the gather passes with the CG's epilogue (the blocks resident at
- * once, one wave, or eight blocks per SM; eight only when more than 3% faster).  The choices are stored in the graph and used by every later
- * call with the same (dtype, c); untuned graphs use a 128-column chunk and one-wave
- * grids.  Results of later calls may differ from untuned ones in summation
+ * n, m, c, the panel type and the degree distribution.  The chunks are timed in the
+ * variant the CG launches (for BF16 search directions: FP32 Z, with the column
+ * partials of X.Z), and for the pair residual in both its full and compact forms.  At
+ * the chosen chunk it also times the grid of the gather passes (the blocks resident at
+ * once, one wave, or eight blocks per SM; eight only when more than 3% faster).  The
+ * choices are stored in the graph and used by every later call with the same
+ * (dtype, c); untuned graphs use 512-byte row chunks (64 FP64, 128 FP32 or 256 BF16
+ * columns) and one-wave grids.  Results of later calls may differ from untuned ones in summation
  * order only (each column's sums are unchanged for the operator; the pair residual
  * is FP64-accurate either way).  Allocates and frees temporary panels (3 n x c plus,
- * for FP32/BF16, about 5 n x c floats).
+ * for FP32/BF16, about 6 n x c floats).
  *   w               device FP64[m] weights (sets the graph's degree vectors)
  *   chunk_cols      optional host out: the chosen operator chunk in columns
  *   pair_chunk_cols optional host out: the chosen residual chunk (0 for FP64)
