@@ -245,12 +245,14 @@ def test_cg_mixed_precision(mode):
     assert err.max() <= (1 + wl.lam) / wl.lam * 1e-8 * 1.01 + 1e-12
 
 
-def test_cg_fp32_loose_tol_starts_from_fp32_residual():
-    """At tol >= 4 * 2^-24 * (1 + 2(1+lam)/lam) the FP32 solve starts from an FP32
-    estimate of the first residual; convergence is still decided on the FP64-accurate
-    residual: the reported relres matches the host's FP64 residual of the returned F,
-    and a warm start from a converged F ends without iterations (the estimate alone
-    never ends a solve)."""
+@pytest.mark.parametrize("mode", [hgl.HGL_FP32, hgl.HGL_BF16])
+def test_cg_fp32_loose_tol_starts_from_fp32_residual(mode):
+    """At tol >= 4 * 2^-24 * (1 + 2(1+lam)/lam) the mixed solve (FP32 or BF16 search
+    directions) starts from an FP32 estimate of the first residual and checks with the
+    compact pair residual (low parts in BF16); convergence is still decided on an
+    FP64-accurate residual: the reported relres matches the host's FP64 residual of the
+    returned F, and a warm start from a converged F ends without iterations (the
+    estimate alone never ends a solve)."""
     wl, d, og, H = _case("mixed_cg", 4, n=9000, m=14000, c=21)
     tol = 3e-6
     assert tol >= 4 * 2.0 ** -24 * (1 + 2 * (1 + wl.lam) / wl.lam)
@@ -259,7 +261,7 @@ def test_cg_fp32_loose_tol_starts_from_fp32_residual():
     g = hgl.build_incidence(d["n"], d["m"], d["edge_ptr"], d["members"])
     wt = torch.tensor(w, device=DEV)
     Y = _panel(d["Y"])
-    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=tol, dtype=hgl.HGL_FP32)
+    F, relres, iters, st = hgl.cg_solve(g, wt, wl.lam, Y, tol=tol, dtype=mode)
     Fg = F.cpu().numpy()
     R = wl.lam * d["Y"] - core.theta_apply(H, w, Fg, 1.0 + wl.lam, -1.0)
     rel = np.linalg.norm(R, axis=0) / np.linalg.norm(wl.lam * d["Y"], axis=0)
@@ -267,7 +269,7 @@ def test_cg_fp32_loose_tol_starts_from_fp32_residual():
     assert np.allclose(relres.cpu().numpy(), rel, rtol=1e-3, atol=1e-12)
     ref, _ = core.certified_solve(H, w, wl.lam, d["Y"])
     assert _relcol(Fg, ref).max() <= (1 + wl.lam) / wl.lam * tol * 1.01
-    F2, relres2, iters2, st2 = hgl.cg_solve(g, wt, wl.lam, Y, F=F, tol=tol, dtype=hgl.HGL_FP32, warm_start=True)
+    F2, relres2, iters2, st2 = hgl.cg_solve(g, wt, wl.lam, Y, F=F, tol=tol, dtype=mode, warm_start=True)
     assert iters2.cpu().numpy().max() == 0 and st2.refinements == 0
     assert np.allclose(relres2.cpu().numpy(), rel, rtol=1e-3, atol=1e-12)
     assert np.array_equal(F2.cpu().numpy(), Fg)

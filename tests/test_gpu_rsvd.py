@@ -384,7 +384,8 @@ def test_captured_step_keeps_block_pattern_and_matches_fresh_build():
     assert int((wt == 0).sum()) > 0  # the steps zeroed weights: entries of the pattern went to 0
 
 
-def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs():
+@pytest.mark.parametrize("dtype", [hgl.HGL_FP32, hgl.HGL_BF16])
+def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs(dtype):
     """With eta = 0 the weights stay put, so from the second step on the warm-started F
     already meets tol and the captured solve skips its sweeps; at tol = 3e-6 it starts
     from an FP32 estimate of the residual, and the relres it reports must still be the
@@ -397,7 +398,7 @@ def test_captured_step_reports_fp64_accurate_relres_when_no_sweep_runs():
     den = np.linalg.norm(wl.lam * d["Y"], axis=0)
     for i in range(4):
         w_before = wt.cpu().numpy().copy()
-        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 0.0, 0.0, tol=tol, dtype=hgl.HGL_FP32,
+        st = hgl.adaptive_step(g, wt, Y, F, wl.lam, 0.0, 0.0, tol=tol, dtype=dtype,
                                route=hgl.HGL_ROUTE_BR, block_ptr=d["block_ptr"], k=16, p=8, q=2,
                                seed=SEED + i, flags=hgl.HGL_STEP_GRAPH)
         R = wl.lam * d["Y"] - core.theta_apply(H, w_before, F.cpu().numpy(), 1.0 + wl.lam, -1.0)
