@@ -58,6 +58,12 @@ template <> __device__ __forceinline__ double to_double<double>(double x) { retu
 
 // storage <-> accumulation type of the block assembly (no FP64 step for FP32 sums)
 template <class TA> __device__ __forceinline__ TA from_acc(double x) { return from_double<TA>(x); }
+// An FP32 or FP64 basis entry into the transposed basis' type (FP32 -> BF16 directly: the
+// same rounding as through FP64, without two conversions on the slow FP64 pipe).
+template <class TB, class T> __device__ __forceinline__ TB basis_from(T x) { return from_double<TB>((double)x); }
+template <> __device__ __forceinline__ __nv_bfloat16 basis_from<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
 template <class TA> __device__ __forceinline__ TA from_acc(float x);
 template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) {
   return __float2bfloat16_rn(x);
@@ -794,7 +800,7 @@ __global__ void __launch_bounds__(256) k_apply_rinv(Blocks B, const int32_t* __r
       const int64_t kb0 = B.koff[b] + i0;
       for (int q = threadIdx.x; q < LPAD * TR; q += blockDim.x) {
         const int j = q / TR, rr = q % TR;
-        if (rr < nr) St[(int64_t)j * B.Ktot + kb0 + rr] = from_double<TB>((double)sy[rr * LS + j]);
+        if (rr < nr) St[(int64_t)j * B.Ktot + kb0 + rr] = basis_from<TB, T>(sy[rr * LS + j]);
       }
     }
     __syncthreads();
