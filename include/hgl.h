@@ -110,11 +110,12 @@ hgl_status hgl_selftest_wait_timeout(int64_t limit_cycles, void* stream);
 /*
  * hgl_selftest_pair_split -- the conversions between an FP64 panel and the FP32 pair
  * (hi, lo) that the mixed-precision solver keeps its iterate in (refinement around an
- * FP32 CG; the benchmark spec's FP64 residual recomputation), run on given values: for each
+ * FP32 CG whose residual is recomputed FP64-accurately), run on given values: for each
  * i, hi[i] = x[i] rounded to FP32 (nearest-even), lo[i] = x[i] - hi[i] rounded to FP32,
  * back[i] = (double)hi[i] + (double)lo[i] in FP64.  The solver computes these from the
  * IEEE-754 bit fields (no FP64 arithmetic in range) and this call exposes them for a test
- * against the plain FP64 definitions.
+ * against the plain FP64 definitions.  The paper has no counterpart: the refinement
+ * around a low-precision CG is this library's way of reaching FP64 accuracy.
  *   x     device FP64[len];  hi, lo  device FP32[len];  back  device FP64[len]
  * Asynchronous on `stream`.  Errors: HGL_ERR_INVALID_ARG (NULL arrays, len < 0).
  */
