@@ -165,3 +165,39 @@ def test_theta_rows_matches_the_sparse_operator():
     Z = theta_rows(lists, w, lambda u: X[np.asarray(u)], rows, 1.5, -1.0)
     ref = theta_apply(H, w, X, 1.5, -1.0)[rows]
     assert np.allclose(Z, ref, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_split_by_hyperedge_size_is_eq1(seed):
+    """The GPU operator splits Eq. 1 by hyperedge size: hyperedges of more than three
+    members go through the intermediate t_e H^T s X, the others become vertex-to-vertex
+    terms -- per member u of such a hyperedge, t_e s_v X[v] for its other members v plus
+    the diagonal s_u^2 t_e X[u].  Written out here with explicit loops, the two parts add
+    up to the oracle's Theta X (any split threshold, sizes one to six, a vertex in no
+    hyperedge)."""
+    rng = np.random.default_rng(300 + seed)
+    n, m, c = 40, 60, 3
+    sizes = rng.integers(1, 7, m)
+    mem = np.concatenate([rng.choice(n - 1, int(k), replace=False) for k in sizes]).astype(np.int32)
+    ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(sizes, out=ptr[1:])
+    w = rng.random(m) + 0.05
+    X = rng.standard_normal((n, c))
+    H = _H(n, m, ptr, mem)
+    _, _, s, t = degrees(H, w)
+    for small in (0, 3, 6):
+        Z = np.zeros((n, c))
+        for e in range(m):
+            vs = [int(v) for v in mem[ptr[e]:ptr[e + 1]]]
+            if len(vs) > small:   # through the intermediate
+                T = t[e] * sum(s[v] * X[v] for v in vs)
+                for u in vs:
+                    Z[u] += s[u] * T
+            else:                 # vertex-to-vertex terms and the diagonal
+                for u in vs:
+                    Z[u] += s[u] * s[u] * t[e] * X[u]
+                    for v in vs:
+                        if v != u:
+                            Z[u] += s[u] * t[e] * s[v] * X[v]
+        assert np.allclose(Z, theta_apply(H, w, X), rtol=1e-13, atol=1e-15)
+        assert np.all(Z[n - 1] == 0.0)
