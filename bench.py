@@ -208,8 +208,9 @@ def bytes_gradient(n, m, nnz, c):
 
 
 # CG iterations per outer iteration of the GPU loop on this workload (its mean over a
-# 20-iteration loop, 9.9); the oracle's sampled step is scaled to this many
-REF_ITERS_PER_STEP = 10.0
+# 20-iteration loop: 7.0 on the BR route, 6.35 for the plain FP64 CG); the oracle's
+# sampled step is scaled to this many
+REF_ITERS_PER_STEP = 7.0
 
 
 def oracle_prepare(d):
