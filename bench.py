@@ -47,7 +47,7 @@ SEED = 20190822
 # the full workload at a given panel type and column chunk, from one ncu capture of this
 # bench (summarised under profiles/); reported as roofline.traffic only for a run of that
 # workload with that chunk.
-NCU_TRAFFIC_PER_LAUNCH = {("operator", "bf16", 256): 46.3e9}
+NCU_TRAFFIC_PER_LAUNCH = {("operator", "bf16", 256): 49.15e9}
 LOOP = 20           # outer iterations of one adaptive loop
 K_RANK, P_OVER, Q_ITERS = 64, 10, 2
 BCG_S, BCG_STEPS = 32, 4   # block CG comparator: columns per group, outer iterations timed

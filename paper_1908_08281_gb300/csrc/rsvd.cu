@@ -273,8 +273,12 @@ template <class T, int LP>
 hgl_status gram(const Work& w, const T* X, const T* Y, cudaStream_t st) {
   const int nb = w.B.nb;
   hgl::count_launch(2);
-  rsvd::k_gram_part<T, LP><<<nb * w.max_splits, 256, 0, st>>>(w.B, w.max_splits, X, Y, w.Gpart);
-  rsvd::k_gram_reduce<LP><<<nb, 256, 0, st>>>(w.B, w.max_splits, w.Gpart, w.G);
+  const bool sym = X == Y;
+  if (sym)
+    rsvd::k_gram_part<T, LP, true><<<nb * w.max_splits, 256, 0, st>>>(w.B, w.max_splits, X, Y, w.Gpart);
+  else
+    rsvd::k_gram_part<T, LP, false><<<nb * w.max_splits, 256, 0, st>>>(w.B, w.max_splits, X, Y, w.Gpart);
+  rsvd::k_gram_reduce<LP><<<nb, 256, 0, st>>>(w.B, w.max_splits, w.Gpart, w.G, sym);
   HGL_CHECK_CUDA(cudaGetLastError());
   return HGL_OK;
 }

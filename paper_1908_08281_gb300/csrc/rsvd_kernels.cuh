@@ -575,7 +575,10 @@ template <> struct GramAcc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-template <class T, int LPAD>
+// SYM (X == Y): only the 16 x 16 tiles on and above the diagonal are formed (15 of 25 for
+// LPAD = 80); k_gram_reduce mirrors the others.  Products commute, so the mirrored
+// entries are the ones a full pass would form.
+template <class T, int LPAD, bool SYM>
 __global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, const T* __restrict__ X,
                                                     const T* __restrict__ Y, double* __restrict__ Gpart) {
   constexpr int TR = sizeof(T) == 8 ? 32 : 64;
@@ -614,28 +617,35 @@ __global__ void __launch_bounds__(256) k_gram_part(Blocks B, int max_splits, con
 #pragma unroll
       for (int a = 0; a < TT; ++a)
 #pragma unroll
-        for (int c = 0; c < TT; ++c) part[a][c] = fma(xv[a], yv[c], part[a][c]);
+        for (int c = 0; c < TT; ++c)
+          if (!SYM || a <= c) part[a][c] = fma(xv[a], yv[c], part[a][c]);
     }
 #pragma unroll
     for (int a = 0; a < TT; ++a)
 #pragma unroll
-      for (int c = 0; c < TT; ++c) acc[a][c].add(part[a][c]);
+      for (int c = 0; c < TT; ++c)
+        if (!SYM || a <= c) acc[a][c].add(part[a][c]);
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < TT; ++a)
 #pragma unroll
-    for (int c = 0; c < TT; ++c) out[(ty + 16 * a) * LPAD + tx + 16 * c] = acc[a][c].value();
+    for (int c = 0; c < TT; ++c)
+      if (!SYM || a <= c) out[(ty + 16 * a) * LPAD + tx + 16 * c] = acc[a][c].value();
 }
 
-// G[b] = sum of the block's partial Grams in range order
+// G[b] = sum of the block's partial Grams in range order (sym: the entries below the
+// diagonal's 16 x 16 tiles from their mirror images)
 template <int LPAD>
-__global__ void k_gram_reduce(Blocks B, int max_splits, const double* __restrict__ Gpart, double* __restrict__ G) {
+__global__ void k_gram_reduce(Blocks B, int max_splits, const double* __restrict__ Gpart, double* __restrict__ G,
+                              bool sym) {
   const int b = blockIdx.x;
   const int nsplit = (B.rows[b] + GRAM_SPLIT - 1) / GRAM_SPLIT;
   for (int q = threadIdx.x; q < LPAD * LPAD; q += blockDim.x) {
+    const int i = q / LPAD, j = q % LPAD;
+    const int src = sym && (i >> 4) > (j >> 4) ? j * LPAD + i : q;
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += Gpart[((int64_t)b * max_splits + sp) * LPAD * LPAD + q];
+    for (int sp = 0; sp < nsplit; ++sp) s += Gpart[((int64_t)b * max_splits + sp) * LPAD * LPAD + src];
     G[(int64_t)b * LPAD * LPAD + q] = s;
   }
 }

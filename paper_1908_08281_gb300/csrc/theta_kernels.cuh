@@ -198,8 +198,13 @@ k_edge_pass(int64_t m, const int64_t* __restrict__ csc_ptr, const int32_t* __res
   }
 }
 
+// The CG's variant with BF16 search directions and one vector per lane is bounded to
+// five resident blocks per SM (48 registers instead of 64, 48 bytes spilled): its
+// dependent intermediate-row gathers gain more from the extra warps than the spills cost
+// (8.62 against 8.88 ms per apply at n = 1M, c = 512); the other variants keep the
+// compiler's choice (wider tiles would spill hundreds of bytes).
 template <class TX, class TT, class TZ, int LG, int NV, int EPI>
-__global__ void __launch_bounds__(OP_THREADS)
+__global__ void __launch_bounds__(OP_THREADS, (sizeof(TX) == 2 && EPI == EPI_DOT_XZ && NV == 1) ? 5 : 1)
 k_vertex_pass(int64_t n, const int64_t* __restrict__ csr_ptr, const int32_t* __restrict__ csr_idx,
               const SmallTerms<typename AccOf<TX>::type> sm,
               const typename AccOf<TX>::type* __restrict__ s, const TT* __restrict__ Tp, int64_t ldt, const TX* __restrict__ X,
